@@ -1,0 +1,173 @@
+/*
+ * overlap.h -- C ABI of the GB300 (sm_103a) overlap Dirac operator library.
+ *
+ * Operator (Cundy & Lee, "Overlap fermions on GPUs", arXiv:1510.06897):
+ *
+ *   D[mu]   = 1/2 (1 + mu + (1 - mu) gamma5 sign(K))                               (Eq. 1)
+ *   K       = gamma5 (D_W - m_W),  m_W = 1.5                                        (Sec. 2)
+ *   D_W psi = 4 psi(x) - 1/2 sum_mu [(1 - gamma_mu) U_mu(x) psi(x+mu^)
+ *                                  + (1 + gamma_mu) U_mu(x-mu^)^dagger psi(x-mu^)] (Eq. 2)
+ *   sign(K) = sum_m alpha_m T_m(K)
+ *             + sum_i phi_i phi_i^dagger [sign(lambda_i) - sum_m alpha_m T_m(lambda_i)] (Eq. 3)
+ *
+ * Reading of Eq. 3 used by every call: the polynomial is P(K) = K f_N(K^2), with
+ * f_N the order-N Chebyshev interpolant of y^{-1/2} on [lo^2, hi^2] (N + 1
+ * coefficients, 2N + 1 applications of K per sign apply), and the deflation is
+ * applied in projected form: sign(K) psi = P(K)(1 - Phi Phi^dagger) psi
+ * + sum_i sign(lambda_i) phi_i phi_i^dagger psi (equal to Eq. 3 for exact
+ * eigenvectors).  Gamma basis: chiral (DeGrand-Rossi), gamma5 = diag(1,1,-1,-1).
+ *
+ * Layouts (all interface arrays are AoS, little-endian, C order):
+ *   dims     = {Lx, Ly, Lz, Lt}, each >= 2; V = Lx Ly Lz Lt; site index
+ *              s = ((t*Lz + z)*Ly + y)*Lx + x.
+ *   links    complex128 [4][V][3][3]: U_mu(s) on the link s -> s+mu^, mu = x,y,z,t,
+ *              colour matrix row-major.  Must be SU(3) to rounding (rows 0 and 1
+ *              are stored in FP32/FP16/BF16 operators, row 2 is rebuilt).
+ *   spinors  complex128 (OV_C128) or complex64 (OV_C64) [nrhs][V][4][3],
+ *              [spin][colour] per site.
+ *   evecs    complex128 [n_ev][V][4][3], orthonormal eigenvectors of K.
+ *
+ * Pointers: every vector / link / evec pointer may be a device pointer or a
+ * host pointer (detected with cudaPointerGetAttributes; host data is staged
+ * through a context-owned device buffer with cudaMemcpyAsync).  Caller-owned
+ * memory is never retained after a call returns.  All work is issued on the
+ * stream given to ov_create; calls return after the result is complete.
+ *
+ * Errors: every call returns an ov_status; ov_last_error() gives a one-line
+ * description of the last failure on that context.  Invalid arguments are
+ * rejected before any device work.  A CUDA failure returns OV_ERR_CUDA.  No
+ * kernel in the library waits on another block or on the host, so no call can
+ * hang the device.
+ *
+ * Precisions (ov_create):
+ *   OV_FP64        links (18 reals) and vectors FP64, FP64 arithmetic.
+ *   OV_FP32        links reconstruct-12 and vectors FP32, FP32 arithmetic,
+ *                  FP64 global sums.
+ *   OV_MIXED_FP16  links reconstruct-12 and recurrence vectors FP16, FP32
+ *                  arithmetic; deflation, assembly and solver inner vectors FP32.
+ *   OV_MIXED_BF16  as OV_MIXED_FP16 with BF16 storage.
+ * ov_wilson / ov_kernel / ov_sign* / ov_overlap run in the context's precision.
+ * ov_solve always converges the residual of the FP64 operator (the context
+ * keeps an FP64 copy of links and eigenvectors): OV_FP64 runs plain FP64 CG;
+ * the other precisions run inner CG in their own precision inside an FP64
+ * defect-correction loop.
+ */
+#ifndef OVERLAP_GB300_H
+#define OVERLAP_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ov_ctx ov_ctx;
+
+typedef enum {
+  OV_OK = 0,
+  OV_ERR_INVALID = 1,       /* bad argument (dims, sizes, null pointer, order, interval) */
+  OV_ERR_NOMEM = 2,         /* device allocation failed */
+  OV_ERR_CUDA = 3,          /* a CUDA call or kernel launch failed */
+  OV_ERR_NOT_CONVERGED = 4, /* solver hit maxit; best x and its residual are still returned */
+  OV_ERR_STATE = 5          /* call needs ov_sign_config first */
+} ov_status;
+
+typedef enum { OV_FP64 = 0, OV_FP32 = 1, OV_MIXED_FP16 = 2, OV_MIXED_BF16 = 3 } ov_prec;
+typedef enum { OV_C128 = 0, OV_C64 = 1 } ov_dtype;
+
+/* Per-context counters, reset by ov_reset_stats. */
+typedef struct {
+  long long kernel_launches;   /* all kernels launched by this context */
+  long long dslash_launches;   /* stencil kernels (one K or D_W application each, all RHS) */
+  long long sign_applies;      /* sign(K) applications (per RHS) */
+  long long inner_iterations;  /* CG iterations in the context's precision (last ov_solve) */
+  long long outer_iterations;  /* FP64 defect-correction steps (last ov_solve) */
+} ov_stats;
+
+/* Creates a context for one lattice and gauge field (Eq. 2 links).  Copies and
+ * compresses the links into context-owned device memory (FP64 copy always;
+ * plus the copy in `prec`).  m_w: Wilson mass of the kernel (1.5 in Sec. 2).
+ * antiperiodic_t != 0: fermion boundary condition antiperiodic in t (periodic
+ * otherwise).  cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: OV_ERR_INVALID (null ctx/dims/links, any L < 2, bad prec),
+ * OV_ERR_NOMEM, OV_ERR_CUDA. */
+ov_status ov_create(ov_ctx** ctx, const int dims[4], const void* links, ov_prec prec, double m_w,
+                    int antiperiodic_t, void* cuda_stream);
+
+/* Frees all context-owned device memory.  NULL is accepted. */
+ov_status ov_destroy(ov_ctx* ctx);
+
+/* out = D_W in (Eq. 2), nrhs right-hand sides.  in and out must not overlap. */
+ov_status ov_wilson(ov_ctx* ctx, const void* in, void* out, int nrhs, ov_dtype dtype);
+
+/* out = K in = gamma5 (D_W - m_W) in (Sec. 2). */
+ov_status ov_kernel(ov_ctx* ctx, const void* in, void* out, int nrhs, ov_dtype dtype);
+
+/* Configures sign(K) (Eq. 3): Chebyshev order N >= 1 of f_N on [lo^2, hi^2]
+ * with 0 < lo < hi (lo = |lambda_{n_ev+1}|, hi >= lambda_max of K), and n_ev >= 0
+ * deflated eigenpairs (evals: host array of n_ev doubles; evecs: complex128
+ * [n_ev][V][4][3], may be NULL when n_ev = 0).  The coefficients are computed
+ * on the host in FP64; eigenvectors are copied into context-owned memory in
+ * FP64 and in the context's vector precision.  sign(0) is taken as +1.
+ * Errors: OV_ERR_INVALID, OV_ERR_NOMEM, OV_ERR_CUDA. */
+ov_status ov_sign_config(ov_ctx* ctx, int order, double lo, double hi, const double* evals, const void* evecs,
+                         int n_ev);
+
+/* out = sign(K) in with the configuration of the last ov_sign_config.
+ * OV_ERR_STATE if none. */
+ov_status ov_sign_apply(ov_ctx* ctx, const void* in, void* out, int nrhs, ov_dtype dtype);
+
+/* ov_sign_config followed by ov_sign_apply. */
+ov_status ov_sign(ov_ctx* ctx, int order, double lo, double hi, const double* evals, const void* evecs, int n_ev,
+                  const void* in, void* out, int nrhs, ov_dtype dtype);
+
+/* out = D[mu] in (Eq. 1), or D[mu]^dagger in = 1/2 ((1+mu) in + (1-mu) sign(K) gamma5 in)
+ * when dagger != 0.  Uses the last sign configuration (OV_ERR_STATE if none). */
+ov_status ov_overlap(ov_ctx* ctx, double mu, int dagger, const void* in, void* out, int nrhs, ov_dtype dtype);
+
+/* Solves D[mu]^dagger D[mu] x = D[mu]^dagger b by CG (one solve per RHS, all RHS
+ * advanced together) until ||D^dagger b - D^dagger D x|| / ||D^dagger b|| <= tol
+ * for every RHS, the residual recomputed with the FP64 operator.  x need not be
+ * initialised.  iters (may be NULL): total CG iterations (inner iterations for
+ * mixed precisions).  true_rel_resid (may be NULL): the largest final relative
+ * residual over the RHS.  OV_ERR_NOT_CONVERGED when maxit iterations did not
+ * reach tol (x holds the last iterate).  OV_ERR_STATE without a sign
+ * configuration. */
+ov_status ov_solve(ov_ctx* ctx, double mu, double tol, int maxit, const void* b, void* x, int nrhs,
+                   ov_dtype dtype, int* iters, double* true_rel_resid);
+
+/* Inner-solver controls for the mixed-precision defect correction: relative
+ * tolerance of each inner solve (default 1e-5) and the maximum number of FP64
+ * outer steps (default 30). */
+ov_status ov_set_solver_params(ov_ctx* ctx, double inner_tol, int max_outer);
+
+/* Computes the n_ev eigenpairs of K of smallest |lambda| (the input of the
+ * deflation in Eq. 3; Sec. 2 uses a polynomial-preconditioned Lanczos), by
+ * Chebyshev-filtered block subspace iteration on K^2 followed by Rayleigh-Ritz
+ * with K, in FP64 arithmetic for all inner products.  evals: host, n_ev
+ * doubles, ascending |lambda|; evecs: complex128 [n_ev][V][4][3] (host or
+ * device).  tol: relative eigen-residual ||K phi - lambda phi|| <= tol * lambda_max.
+ * lambda_max_out (may be NULL): an upper bound of |lambda| of K.
+ * Errors: OV_ERR_INVALID, OV_ERR_NOT_CONVERGED (best pairs returned). */
+ov_status ov_eigs(ov_ctx* ctx, int n_ev, double tol, int max_iter, double* evals, void* evecs,
+                  double* lambda_max_out);
+
+/* Gradient of S = chi^dagger P(K) chi, P(K) = K f_N(K^2) the undeflated
+ * polynomial of Eq. 3 on [lo^2, hi^2], with respect to every link:
+ * grad_links complex128 [4][V][3][3] receives F_mu(x) in su(3) with
+ * dS/deps = sum Re tr(X^dagger F) for U -> exp(eps X) U.  chi: one spinor in
+ * `dtype`.  Runs the recurrence forward with checkpoints every 16 terms, then
+ * backward with recomputation.  Errors: OV_ERR_INVALID. */
+ov_status ov_sign_poly_grad(ov_ctx* ctx, int order, double lo, double hi, const void* chi, void* grad_links,
+                            ov_dtype dtype);
+
+ov_status ov_get_stats(const ov_ctx* ctx, ov_stats* out);
+ov_status ov_reset_stats(ov_ctx* ctx);
+
+/* Last error message of the context ("" if none); never NULL.  Passing NULL
+ * returns the message of the last failed ov_create on this thread. */
+const char* ov_last_error(const ov_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OVERLAP_GB300_H */

@@ -1,0 +1,723 @@
+// C ABI of the overlap library: context, argument checks, host/device
+// staging, the sign(K) driver (deflation, Chebyshev recurrence, fused
+// assembly), the overlap operator and the CG solver.  All arithmetic runs in
+// the kernels of dslash.cu / blas.cu; this file only sequences launches and
+// reads back FP64 scalars for the solver.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/overlap.h"
+#include "internal.h"
+
+using namespace ov;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t n) {
+    if (n <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e == cudaSuccess) bytes = n;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T> T* as() const { return static_cast<T*>(p); }
+  char* c() const { return static_cast<char*>(p); }
+};
+
+// One operator instance: links, eigenvectors and work vectors in one precision.
+struct Inst {
+  OpPrec p = OP_F64;   // link / recurrence storage
+  OpPrec pv = OP_F64;  // vector storage: deflation, assembly, solver vectors
+  bool active = false;
+  DevBuf links, evecs;
+  DevBuf xin, xout, d, tmp;          // pv
+  DevBuf perp, t, bA, bB;            // p
+  DevBuf cx, cr, cp, cq;             // pv: inner CG
+  size_t vbytes(int64_t V) const { return (size_t)spinor_bytes_per_site(pv) * V; }
+  size_t pbytes(int64_t V) const { return (size_t)spinor_bytes_per_site(p) * V; }
+  void release() {
+    for (DevBuf* b : {&links, &evecs, &xin, &xout, &d, &tmp, &perp, &t, &bA, &bB, &cx, &cr, &cp, &cq}) b->release();
+  }
+};
+
+enum Kind { K_SIGN, K_OVL, K_OVL_DAG };
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct ov_ctx {
+  LatticeH g{};
+  double m_w = 1.5;
+  cudaStream_t st = nullptr;
+  ov_prec prec = OV_FP64;
+  Inst hi;  // FP64 operator (always)
+  Inst lo;  // operator in the context precision when it is not FP64
+  // sign configuration
+  bool configured = false;
+  int order = 0;
+  double a = 0, b = 0;
+  std::vector<double> coef;
+  int n_ev = 0;
+  std::vector<double> evals, sgn;
+  DevBuf d_sgn, d_c, d_partial, d_scalars;
+  DevBuf stage_in, stage_out, stage_links;
+  DevBuf o_x, o_r, o_rhs, o_q;  // FP64 outer-solver vectors
+  double* h_scalars = nullptr;  // pinned
+  int h_scalars_n = 0;
+  // solver controls
+  double inner_tol = 1e-5;
+  int max_outer = 30;
+  ov_stats stats{};
+  std::string err;
+
+  Inst& op() { return prec == OV_FP64 ? hi : lo; }
+};
+
+namespace {
+
+ov_status fail(ov_ctx* c, ov_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define OV_CK(call)                                                                             \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? OV_ERR_NOMEM : OV_ERR_CUDA,              \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                          \
+  } while (0)
+
+#define OV_TRY(expr)              \
+  do {                            \
+    ov_status s_ = (expr);        \
+    if (s_ != OV_OK) return s_;   \
+  } while (0)
+
+inline ov_status launched(ov_ctx* c, int n = 1) {
+  c->stats.kernel_launches += n;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, OV_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return OV_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller input: the pointer itself, or a staged copy.
+ov_status stage_in(ov_ctx* c, DevBuf& buf, const void* p, size_t bytes, const void** out) {
+  if (is_device_ptr(p)) {
+    *out = p;
+    return OV_OK;
+  }
+  OV_CK(buf.ensure(bytes));
+  OV_CK(cudaMemcpyAsync(buf.p, p, bytes, cudaMemcpyHostToDevice, c->st));
+  *out = buf.p;
+  return OV_OK;
+}
+
+// Device destination for a caller output; finish_out copies it back if needed.
+ov_status stage_out(ov_ctx* c, void* p, size_t bytes, void** out, bool* staged) {
+  if (is_device_ptr(p)) {
+    *out = p;
+    *staged = false;
+    return OV_OK;
+  }
+  OV_CK(c->stage_out.ensure(bytes));
+  *out = c->stage_out.p;
+  *staged = true;
+  return OV_OK;
+}
+
+ov_status finish_out(ov_ctx* c, void* host, size_t bytes, bool staged) {
+  if (staged) OV_CK(cudaMemcpyAsync(host, c->stage_out.p, bytes, cudaMemcpyDeviceToHost, c->st));
+  OV_CK(cudaStreamSynchronize(c->st));
+  return OV_OK;
+}
+
+size_t iface_bytes(const LatticeH& g, int nrhs, ov_dtype dt) {
+  return (size_t)g.V * nrhs * 12 * (dt == OV_C128 ? 16 : 8);
+}
+
+ov_status ensure_scalars(ov_ctx* c, int n) {
+  if (c->h_scalars_n < n) {
+    if (c->h_scalars) cudaFreeHost(c->h_scalars);
+    c->h_scalars = nullptr;
+    c->h_scalars_n = 0;
+    OV_CK(cudaMallocHost(&c->h_scalars, sizeof(double2) * n));
+    c->h_scalars_n = n;
+  }
+  OV_CK(c->d_scalars.ensure(sizeof(double2) * n));
+  return OV_OK;
+}
+
+// Reads back n double2 values reduced from partial sums.
+ov_status read_reduced(ov_ctx* c, const double2* partial, int n, double2* out) {
+  OV_TRY(ensure_scalars(c, n));
+  launch_reduce_partials(partial, n, kReduceBlocks, c->d_scalars.as<double2>(), c->st);
+  OV_TRY(launched(c));
+  OV_CK(cudaMemcpyAsync(c->h_scalars, c->d_scalars.p, sizeof(double2) * n, cudaMemcpyDeviceToHost, c->st));
+  OV_CK(cudaStreamSynchronize(c->st));
+  std::memcpy(out, c->h_scalars, sizeof(double2) * n);
+  return OV_OK;
+}
+
+ov_status ensure_work(ov_ctx* c, Inst& I, int nrhs) {
+  const int64_t V = c->g.V;
+  const size_t vb = I.vbytes(V) * nrhs, pb = I.pbytes(V) * nrhs;
+  OV_CK(I.xin.ensure(vb));
+  OV_CK(I.xout.ensure(vb));
+  OV_CK(I.d.ensure(vb));
+  OV_CK(I.tmp.ensure(vb));
+  OV_CK(I.perp.ensure(pb));
+  OV_CK(I.t.ensure(pb));
+  OV_CK(I.bA.ensure(pb));
+  OV_CK(I.bB.ensure(pb));
+  OV_CK(c->d_partial.ensure(sizeof(double2) * kReduceBlocks * (size_t)std::max(1, c->n_ev)));
+  OV_CK(c->d_c.ensure(sizeof(double2) * (size_t)std::max(1, c->n_ev) * nrhs));
+  return OV_OK;
+}
+
+// Chebyshev-Gauss interpolation of y^{-1/2} on [a^2, b^2] (Eq. 3 reading):
+// c_j = 2/(N+1) sum_k f(y_k) cos(j theta_k), theta_k = pi (k + 1/2)/(N + 1).
+std::vector<double> chebyshev_coefficients(int order, double a, double b) {
+  const int n1 = order + 1;
+  std::vector<double> f(n1), c(n1);
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < n1; ++k) {
+    const double th = pi * (k + 0.5) / n1;
+    const double y = 0.5 * ((b * b - a * a) * std::cos(th) + b * b + a * a);
+    f[k] = 1.0 / std::sqrt(y);
+  }
+  for (int j = 0; j < n1; ++j) {
+    double s = 0.0;
+    for (int k = 0; k < n1; ++k) s += f[k] * std::cos(j * pi * (k + 0.5) / n1);
+    c[j] = 2.0 * s / n1;
+  }
+  return c;
+}
+
+// K applied to a recurrence vector: out (storage I.p) = s1 K in + sum w_j v_j.
+ov_status k_step(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, const EpiArgs& e) {
+  launch_dslash(I.p, I.p, c->g, I.links.p, in, out, e, nrhs, c->st);
+  c->stats.dslash_launches++;
+  return launched(c);
+}
+
+// sign(K) / D[mu] / D[mu]^dagger on nrhs vectors in I.pv storage.
+// scale: the recurrence runs on scale * (input); results are unscaled in the
+// final epilogue (used to keep 16-bit storage in range).
+ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kind kind, double mu, double scale) {
+  if (!c->configured) return fail(c, OV_ERR_STATE, "sign(K) not configured: call ov_sign_config first");
+  OV_TRY(ensure_work(c, I, nrhs));
+  const int64_t V = c->g.V;
+  const size_t vb = I.vbytes(V), pb = I.pbytes(V);
+  const int g5in = (kind == K_OVL_DAG);
+  const int n_ev = c->n_ev;
+
+  // S3: deflation projection c_i = phi_i^dagger psi, psi_perp = psi - sum c_i phi_i,
+  //     d = sum sgn(lambda_i) c_i phi_i  (both scaled by `scale`)
+  for (int r = 0; r < nrhs; ++r) {
+    const char* in_r = static_cast<const char*>(in) + r * vb;
+    double2* cr = c->d_c.as<double2>() + (size_t)r * std::max(1, n_ev);
+    if (n_ev > 0) {
+      launch_defl_dot(I.pv, c->g, I.evecs.p, n_ev, in_r, g5in, c->d_partial.as<double2>(), c->st);
+      OV_TRY(launched(c));
+      launch_reduce_partials(c->d_partial.as<double2>(), n_ev, kReduceBlocks, cr, c->st);
+      OV_TRY(launched(c));
+    }
+    launch_defl_combine(I.pv, I.p, c->g, I.evecs.p, n_ev, cr, c->d_sgn.as<double>(), in_r, g5in, scale,
+                        I.perp.c() + r * pb, n_ev > 0 ? I.d.c() + r * vb : nullptr, c->st);
+    OV_TRY(launched(c));
+  }
+
+  // S4: backward (Clenshaw) recurrence for f_N(Z) psi_perp, Z = alpha K^2 + beta:
+  //   b_k = c_k psi_perp + 2 Z b_{k+1} - b_{k+2},  k = N-1 .. 1,  b_N = c_N psi_perp,
+  //   h   = (b_0 - b_2)/2 = c_0/2 psi_perp + Z b_1 - b_2.
+  // Each Z application is two stencil launches; the second carries the
+  // recurrence algebra in its epilogue.
+  const double a2 = c->a * c->a, b2 = c->b * c->b;
+  const double alpha = 2.0 / (b2 - a2), beta = -(b2 + a2) / (b2 - a2);
+  const std::vector<double>& cf = c->coef;
+  const int N = c->order;
+  void* perp = I.perp.p;
+  struct Vec {
+    void* p;
+    double s;
+  };
+  Vec b1{perp, cf[N]}, b2v{nullptr, 0.0};
+  void* h = nullptr;
+  for (int k = N - 1; k >= 0; --k) {
+    EpiArgs ek;
+    ek.m_w = c->m_w;
+    OV_TRY(k_step(c, I, b1.p, I.t.p, nrhs, ek));  // t = K b1.p
+    void* dst = (b2v.p != nullptr && b2v.p != perp) ? b2v.p : (b1.p == I.bA.p ? I.bB.p : I.bA.p);
+    EpiArgs e;
+    e.m_w = c->m_w;
+    const double zs = (k > 0) ? 2.0 : 1.0;  // last step builds (b_0 - b_2)/2
+    e.s1 = zs * alpha * b1.s;
+    e.v[0] = b1.p;
+    e.w[0] = zs * beta * b1.s;
+    e.v[1] = b2v.p;
+    e.w[1] = -b2v.s;
+    e.v[2] = perp;
+    e.w[2] = (k > 0) ? cf[k] : 0.5 * cf[0];
+    OV_TRY(k_step(c, I, I.t.p, dst, nrhs, e));
+    b2v = b1;
+    b1 = Vec{dst, 1.0};
+    h = dst;
+  }
+
+  // S5: out = K h (= P(K) psi_perp) + d, with the overlap assembly (Eq. 1) fused:
+  //   sign:   out = (K h + d) / scale
+  //   D:      out = (1+mu)/2 in + (1-mu)/2 gamma5 (K h + d) / scale
+  //   D^dag:  out = (1+mu)/2 in + (1-mu)/2 (K h + d) / scale     (input was gamma5 in)
+  EpiArgs e;
+  e.m_w = c->m_w;
+  const double f = (kind == K_SIGN ? 1.0 : 0.5 * (1.0 - mu)) / scale;
+  e.s1 = f;
+  e.z = n_ev > 0 ? I.d.p : nullptr;
+  e.wz = f;
+  e.g5_out = (kind == K_OVL);
+  if (kind != K_SIGN) {
+    e.y = in;
+    e.c0 = 0.5 * (1.0 + mu);
+  }
+  launch_dslash(I.p, I.pv, c->g, I.links.p, h, out, e, nrhs, c->st);
+  c->stats.dslash_launches++;
+  OV_TRY(launched(c));
+  c->stats.sign_applies += nrhs;
+  return OV_OK;
+}
+
+// out = D^dagger D in (vectors in I.pv), through I.tmp.
+ov_status normal_apply(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, double mu, double scale) {
+  OV_TRY(ensure_work(c, I, nrhs));
+  OV_TRY(sign_core(c, I, in, I.tmp.p, nrhs, K_OVL, mu, scale));
+  return sign_core(c, I, I.tmp.p, out, nrhs, K_OVL_DAG, mu, scale);
+}
+
+ov_status dots(ov_ctx* c, OpPrec p, const void* a, const void* b, int64_t V, double2* out) {
+  launch_dot_partial(p, a, b, V, 1, c->d_partial.as<double2>(), c->st);
+  OV_TRY(launched(c));
+  return read_reduced(c, c->d_partial.as<double2>(), 1, out);
+}
+
+ov_status norm2(ov_ctx* c, OpPrec p, const void* a, int64_t V, double* out) {
+  launch_norm2_partial(p, a, V, 1, c->d_partial.as<double2>(), c->st);
+  OV_TRY(launched(c));
+  double2 r;
+  OV_TRY(read_reduced(c, c->d_partial.as<double2>(), 1, &r));
+  *out = r.x;
+  return OV_OK;
+}
+
+// CG on D^dagger D e = r0 for each RHS, with the operator of instance I;
+// vectors in I.pv.  Stops when |r|/|r0| <= tol for every RHS (iterated
+// residual).  Returns the iteration count in *iters.
+ov_status cg_inner(ov_ctx* c, Inst& I, const void* r0, void* e, int nrhs, double mu, double tol, int maxit,
+                   int* iters) {
+  const int64_t V = c->g.V;
+  const size_t vb = I.vbytes(V) * nrhs, v1 = I.vbytes(V);
+  OV_CK(I.cx.ensure(vb));
+  OV_CK(I.cr.ensure(vb));
+  OV_CK(I.cp.ensure(vb));
+  OV_CK(I.cq.ensure(vb));
+  OV_TRY(ensure_work(c, I, nrhs));
+  OV_CK(cudaMemsetAsync(e, 0, vb, c->st));
+  OV_CK(cudaMemcpyAsync(I.cr.p, r0, vb, cudaMemcpyDeviceToDevice, c->st));
+  OV_CK(cudaMemcpyAsync(I.cp.p, r0, vb, cudaMemcpyDeviceToDevice, c->st));
+  std::vector<double> rr(nrhs), rr0(nrhs);
+  std::vector<char> done(nrhs, 0);
+  for (int r = 0; r < nrhs; ++r) {
+    OV_TRY(norm2(c, I.pv, I.cr.c() + r * v1, V, &rr[r]));
+    rr0[r] = rr[r];
+    if (rr0[r] == 0.0) done[r] = 1;
+  }
+  const bool is16 = (I.p == OP_F16 || I.p == OP_B16);
+  int it = 0;
+  for (; it < maxit; ++it) {
+    bool all = true;
+    for (int r = 0; r < nrhs; ++r) all = all && done[r];
+    if (all) break;
+    double rmax = 0.0;
+    for (int r = 0; r < nrhs; ++r)
+      if (!done[r]) rmax = std::max(rmax, std::sqrt(rr[r]));
+    // keep 16-bit recurrence vectors at O(1) per component
+    const double scale = is16 ? std::sqrt(24.0 * (double)V) / rmax : 1.0;
+    OV_TRY(normal_apply(c, I, I.cp.p, I.cq.p, nrhs, mu, scale));
+    for (int r = 0; r < nrhs; ++r) {
+      if (done[r]) continue;
+      double2 pq;
+      OV_TRY(dots(c, I.pv, I.cp.c() + r * v1, I.cq.c() + r * v1, V, &pq));
+      if (!(pq.x > 0.0) || !std::isfinite(pq.x))
+        return fail(c, OV_ERR_NOT_CONVERGED, "CG breakdown: p^dagger A p <= 0 or not finite");
+      const double alpha = rr[r] / pq.x;
+      launch_cg_update_xr(I.pv, static_cast<char*>(e) + r * v1, I.cr.c() + r * v1, I.cp.c() + r * v1,
+                          I.cq.c() + r * v1, alpha, V, 1, c->d_partial.as<double2>(), c->st);
+      OV_TRY(launched(c));
+      double2 rn;
+      OV_TRY(read_reduced(c, c->d_partial.as<double2>(), 1, &rn));
+      const double beta = rn.x / rr[r];
+      rr[r] = rn.x;
+      if (!std::isfinite(rn.x)) return fail(c, OV_ERR_NOT_CONVERGED, "CG residual not finite");
+      if (std::sqrt(rr[r]) <= tol * std::sqrt(rr0[r])) {
+        done[r] = 1;
+        continue;
+      }
+      launch_cg_update_p(I.pv, I.cp.c() + r * v1, I.cr.c() + r * v1, beta, V, 1, c->st);
+      OV_TRY(launched(c));
+    }
+  }
+  *iters = it;
+  for (int r = 0; r < nrhs; ++r)
+    if (!done[r]) return OV_ERR_NOT_CONVERGED;  // caller decides; no message overwrite
+  return OV_OK;
+}
+
+ov_status check_dtype(ov_ctx* c, int nrhs, ov_dtype dt) {
+  if (nrhs < 1) return fail(c, OV_ERR_INVALID, "nrhs must be >= 1");
+  if (dt != OV_C128 && dt != OV_C64) return fail(c, OV_ERR_INVALID, "dtype must be OV_C128 or OV_C64");
+  return OV_OK;
+}
+
+ov_status pack_input(ov_ctx* c, Inst& I, const void* in, int nrhs, ov_dtype dt, void* dst) {
+  const void* din;
+  OV_TRY(stage_in(c, c->stage_in, in, iface_bytes(c->g, nrhs, dt), &din));
+  launch_pack_spinor(I.pv, dt == OV_C128 ? IF_C128 : IF_C64, c->g, din, dst, nrhs, 1.0, 0, c->st);
+  return launched(c);
+}
+
+ov_status unpack_output(ov_ctx* c, Inst& I, const void* src, void* out, int nrhs, ov_dtype dt) {
+  void* dout;
+  bool staged;
+  const size_t bytes = iface_bytes(c->g, nrhs, dt);
+  OV_TRY(stage_out(c, out, bytes, &dout, &staged));
+  launch_unpack_spinor(I.pv, dt == OV_C128 ? IF_C128 : IF_C64, c->g, src, dout, nrhs, 1.0, c->st);
+  OV_TRY(launched(c));
+  return finish_out(c, out, bytes, staged);
+}
+
+ov_status init_inst(ov_ctx* c, Inst& I, OpPrec p, const void* links_dev) {
+  I.p = p;
+  I.pv = (p == OP_F64) ? OP_F64 : OP_F32;
+  I.active = true;
+  OV_CK(I.links.ensure((size_t)link_bytes_per_site_dir(p) * 4 * c->g.V));
+  launch_pack_links(p, c->g, links_dev, I.links.p, c->st);
+  return launched(c);
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+
+extern "C" {
+
+ov_status ov_create(ov_ctx** ctx, const int dims[4], const void* links, ov_prec prec, double m_w, int antiperiodic_t,
+                    void* cuda_stream) {
+  g_create_error.clear();
+  if (!ctx || !dims || !links) {
+    g_create_error = "ov_create: null argument";
+    return OV_ERR_INVALID;
+  }
+  *ctx = nullptr;
+  int64_t V = 1;
+  for (int i = 0; i < 4; ++i) {
+    if (dims[i] < 2) {
+      g_create_error = "ov_create: every lattice extent must be >= 2";
+      return OV_ERR_INVALID;
+    }
+    V *= dims[i];
+  }
+  if (V > (int64_t(1) << 31) / 16) {
+    g_create_error = "ov_create: lattice too large";
+    return OV_ERR_INVALID;
+  }
+  if (prec < OV_FP64 || prec > OV_MIXED_BF16) {
+    g_create_error = "ov_create: unknown precision";
+    return OV_ERR_INVALID;
+  }
+  if (!std::isfinite(m_w)) {
+    g_create_error = "ov_create: m_w not finite";
+    return OV_ERR_INVALID;
+  }
+  ov_ctx* c = new ov_ctx();
+  for (int i = 0; i < 4; ++i) c->g.L[i] = dims[i];
+  c->g.V = V;
+  c->g.antiperiodic_t = antiperiodic_t ? 1 : 0;
+  c->m_w = m_w;
+  c->prec = prec;
+  c->st = static_cast<cudaStream_t>(cuda_stream);
+  const void* dl = nullptr;
+  ov_status s = stage_in(c, c->stage_links, links, (size_t)V * 4 * 9 * 16, &dl);
+  if (s == OV_OK) s = init_inst(c, c->hi, OP_F64, dl);
+  if (s == OV_OK && prec != OV_FP64) {
+    const OpPrec lp = prec == OV_FP32 ? OP_F32 : prec == OV_MIXED_FP16 ? OP_F16 : OP_B16;
+    s = init_inst(c, c->lo, lp, dl);
+  }
+  if (s == OV_OK) {
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) s = fail(c, OV_ERR_CUDA, cudaGetErrorString(e));
+  }
+  c->stage_links.release();
+  if (s != OV_OK) {
+    g_create_error = c->err;
+    ov_destroy(c);
+    return s;
+  }
+  *ctx = c;
+  return OV_OK;
+}
+
+ov_status ov_destroy(ov_ctx* c) {
+  if (!c) return OV_OK;
+  cudaStreamSynchronize(c->st);
+  c->hi.release();
+  c->lo.release();
+  for (DevBuf* b : {&c->d_sgn, &c->d_c, &c->d_partial, &c->d_scalars, &c->stage_in, &c->stage_out, &c->stage_links,
+                    &c->o_x, &c->o_r, &c->o_rhs, &c->o_q})
+    b->release();
+  if (c->h_scalars) cudaFreeHost(c->h_scalars);
+  delete c;
+  return OV_OK;
+}
+
+static ov_status apply_stencil(ov_ctx* c, const void* in, void* out, int nrhs, ov_dtype dt, int wilson) {
+  if (!c) return OV_ERR_INVALID;
+  if (!in || !out) return fail(c, OV_ERR_INVALID, "null vector");
+  OV_TRY(check_dtype(c, nrhs, dt));
+  Inst& I = c->op();
+  OV_TRY(ensure_work(c, I, nrhs));
+  OV_TRY(pack_input(c, I, in, nrhs, dt, I.xin.p));
+  const void* src = I.xin.p;
+  if (I.p != I.pv) {
+    launch_convert(I.pv, I.p, I.xin.p, I.perp.p, c->g.V, nrhs, 1.0, 0, c->st);
+    OV_TRY(launched(c));
+    src = I.perp.p;
+  }
+  EpiArgs e;
+  e.wilson = wilson;
+  e.m_w = c->m_w;
+  launch_dslash(I.p, I.pv, c->g, I.links.p, src, I.xout.p, e, nrhs, c->st);
+  c->stats.dslash_launches++;
+  OV_TRY(launched(c));
+  return unpack_output(c, I, I.xout.p, out, nrhs, dt);
+}
+
+ov_status ov_wilson(ov_ctx* c, const void* in, void* out, int nrhs, ov_dtype dt) {
+  return apply_stencil(c, in, out, nrhs, dt, 1);
+}
+
+ov_status ov_kernel(ov_ctx* c, const void* in, void* out, int nrhs, ov_dtype dt) {
+  return apply_stencil(c, in, out, nrhs, dt, 0);
+}
+
+ov_status ov_sign_config(ov_ctx* c, int order, double lo, double hi, const double* evals, const void* evecs,
+                         int n_ev) {
+  if (!c) return OV_ERR_INVALID;
+  if (order < 1) return fail(c, OV_ERR_INVALID, "Chebyshev order must be >= 1");
+  if (!(lo > 0.0) || !(hi > lo) || !std::isfinite(hi)) return fail(c, OV_ERR_INVALID, "need 0 < lo < hi");
+  if (n_ev < 0) return fail(c, OV_ERR_INVALID, "n_ev must be >= 0");
+  if (n_ev > 0 && (!evals || !evecs)) return fail(c, OV_ERR_INVALID, "n_ev > 0 needs evals and evecs");
+  for (int i = 0; i < n_ev; ++i)
+    if (!std::isfinite(evals[i])) return fail(c, OV_ERR_INVALID, "eigenvalue not finite");
+  c->configured = false;
+  c->order = order;
+  c->a = lo;
+  c->b = hi;
+  c->coef = chebyshev_coefficients(order, lo, hi);
+  c->n_ev = n_ev;
+  c->evals.assign(evals, evals + n_ev);
+  c->sgn.resize(n_ev);
+  for (int i = 0; i < n_ev; ++i) c->sgn[i] = evals[i] >= 0.0 ? 1.0 : -1.0;
+  OV_CK(c->d_sgn.ensure(sizeof(double) * std::max(1, n_ev)));
+  if (n_ev > 0) {
+    OV_CK(cudaMemcpyAsync(c->d_sgn.p, c->sgn.data(), sizeof(double) * n_ev, cudaMemcpyHostToDevice, c->st));
+    const size_t ib = iface_bytes(c->g, n_ev, OV_C128);
+    const void* de;
+    OV_TRY(stage_in(c, c->stage_in, evecs, ib, &de));
+    for (Inst* I : {&c->hi, &c->lo}) {
+      if (!I->active) continue;
+      OV_CK(I->evecs.ensure(I->vbytes(c->g.V) * n_ev));
+      launch_pack_spinor(I->pv, IF_C128, c->g, de, I->evecs.p, n_ev, 1.0, 0, c->st);
+      OV_TRY(launched(c));
+    }
+    c->stage_in.release();
+  }
+  OV_CK(cudaStreamSynchronize(c->st));
+  c->configured = true;
+  return OV_OK;
+}
+
+ov_status ov_sign_apply(ov_ctx* c, const void* in, void* out, int nrhs, ov_dtype dt) {
+  if (!c) return OV_ERR_INVALID;
+  if (!in || !out) return fail(c, OV_ERR_INVALID, "null vector");
+  OV_TRY(check_dtype(c, nrhs, dt));
+  if (!c->configured) return fail(c, OV_ERR_STATE, "sign(K) not configured: call ov_sign_config first");
+  Inst& I = c->op();
+  OV_TRY(ensure_work(c, I, nrhs));
+  OV_TRY(pack_input(c, I, in, nrhs, dt, I.xin.p));
+  OV_TRY(sign_core(c, I, I.xin.p, I.xout.p, nrhs, K_SIGN, 0.0, 1.0));
+  return unpack_output(c, I, I.xout.p, out, nrhs, dt);
+}
+
+ov_status ov_sign(ov_ctx* c, int order, double lo, double hi, const double* evals, const void* evecs, int n_ev,
+                  const void* in, void* out, int nrhs, ov_dtype dt) {
+  OV_TRY(ov_sign_config(c, order, lo, hi, evals, evecs, n_ev));
+  return ov_sign_apply(c, in, out, nrhs, dt);
+}
+
+ov_status ov_overlap(ov_ctx* c, double mu, int dagger, const void* in, void* out, int nrhs, ov_dtype dt) {
+  if (!c) return OV_ERR_INVALID;
+  if (!in || !out) return fail(c, OV_ERR_INVALID, "null vector");
+  if (!std::isfinite(mu)) return fail(c, OV_ERR_INVALID, "mu not finite");
+  OV_TRY(check_dtype(c, nrhs, dt));
+  if (!c->configured) return fail(c, OV_ERR_STATE, "sign(K) not configured: call ov_sign_config first");
+  Inst& I = c->op();
+  OV_TRY(ensure_work(c, I, nrhs));
+  OV_TRY(pack_input(c, I, in, nrhs, dt, I.xin.p));
+  OV_TRY(sign_core(c, I, I.xin.p, I.xout.p, nrhs, dagger ? K_OVL_DAG : K_OVL, mu, 1.0));
+  return unpack_output(c, I, I.xout.p, out, nrhs, dt);
+}
+
+ov_status ov_set_solver_params(ov_ctx* c, double inner_tol, int max_outer) {
+  if (!c) return OV_ERR_INVALID;
+  if (!(inner_tol > 0.0 && inner_tol < 1.0) || max_outer < 1)
+    return fail(c, OV_ERR_INVALID, "need 0 < inner_tol < 1 and max_outer >= 1");
+  c->inner_tol = inner_tol;
+  c->max_outer = max_outer;
+  return OV_OK;
+}
+
+ov_status ov_solve(ov_ctx* c, double mu, double tol, int maxit, const void* b, void* x, int nrhs, ov_dtype dt,
+                   int* iters, double* true_rel_resid) {
+  if (!c) return OV_ERR_INVALID;
+  if (!b || !x) return fail(c, OV_ERR_INVALID, "null vector");
+  if (!std::isfinite(mu) || !(tol > 0.0) || maxit < 1)
+    return fail(c, OV_ERR_INVALID, "need finite mu, tol > 0, maxit >= 1");
+  OV_TRY(check_dtype(c, nrhs, dt));
+  if (!c->configured) return fail(c, OV_ERR_STATE, "sign(K) not configured: call ov_sign_config first");
+  c->stats.inner_iterations = 0;
+  c->stats.outer_iterations = 0;
+  Inst& H = c->hi;
+  // inner solver: FP64 itself, or the context-precision operator
+  Inst& I = (c->prec == OV_FP64) ? c->hi : c->lo;
+  const int64_t V = c->g.V;
+  const size_t v1 = H.vbytes(V), vb = v1 * nrhs;
+  const size_t iv1 = I.vbytes(V);
+  OV_TRY(ensure_work(c, H, nrhs));
+  OV_TRY(ensure_work(c, I, nrhs));
+  OV_CK(c->o_x.ensure(vb));
+  OV_CK(c->o_r.ensure(vb));
+  OV_CK(c->o_rhs.ensure(vb));
+  OV_CK(c->o_q.ensure(vb));
+  OV_CK(I.cx.ensure(iv1 * nrhs));
+  // rhs = D^dagger b with the FP64 operator
+  OV_TRY(pack_input(c, H, b, nrhs, dt, H.xin.p));
+  OV_TRY(sign_core(c, H, H.xin.p, c->o_rhs.p, nrhs, K_OVL_DAG, mu, 1.0));
+  std::vector<double> rhs_n(nrhs), res(nrhs), rn(nrhs);
+  for (int r = 0; r < nrhs; ++r) {
+    OV_TRY(norm2(c, OP_F64, c->o_rhs.c() + r * v1, V, &rhs_n[r]));
+    rhs_n[r] = std::sqrt(rhs_n[r]);
+    res[r] = rhs_n[r] > 0 ? 1.0 : 0.0;
+    rn[r] = rhs_n[r];
+  }
+  OV_CK(cudaMemsetAsync(c->o_x.p, 0, vb, c->st));
+  OV_CK(cudaMemcpyAsync(c->o_r.p, c->o_rhs.p, vb, cudaMemcpyDeviceToDevice, c->st));
+
+  // Defect correction: r = rhs - A x (FP64), solve A e = r / |r| with inner CG,
+  // x += |r| e, recompute r.  With an FP64 inner solver the first pass usually
+  // meets tol already; the loop then only confirms it.
+  const int max_outer = (c->prec == OV_FP64) ? 4 : c->max_outer;
+  int total = 0;
+  bool ok = false;
+  for (int outer = 0; outer < max_outer; ++outer) {
+    double worst = 0;
+    for (double v : res) worst = std::max(worst, v);
+    if (worst <= tol) {
+      ok = true;
+      break;
+    }
+    if (total >= maxit) break;
+    for (int r = 0; r < nrhs; ++r) {
+      launch_convert(OP_F64, I.pv, c->o_r.c() + r * v1, I.xin.c() + r * iv1, V, 1, rn[r] > 0 ? 1.0 / rn[r] : 0.0,
+                     0, c->st);
+      OV_TRY(launched(c));
+    }
+    double inner = 0.5 * tol / worst;
+    if (c->prec != OV_FP64) inner = std::max(inner, c->inner_tol);
+    inner = std::min(inner, 0.5);
+    int it = 0;
+    ov_status s = cg_inner(c, I, I.xin.p, I.cx.p, nrhs, mu, inner, maxit - total, &it);
+    total += it;
+    if (s != OV_OK && s != OV_ERR_NOT_CONVERGED) return s;
+    for (int r = 0; r < nrhs; ++r) {
+      launch_convert(I.pv, OP_F64, I.cx.c() + r * iv1, c->o_x.c() + r * v1, V, 1, rn[r], 1, c->st);
+      OV_TRY(launched(c));
+    }
+    c->stats.outer_iterations++;
+    // true residual with the FP64 operator
+    OV_TRY(normal_apply(c, H, c->o_x.p, c->o_q.p, nrhs, mu, 1.0));
+    launch_axpby(OP_F64, 1.0, c->o_rhs.p, -1.0, c->o_q.p, c->o_r.p, V, nrhs, c->st);
+    OV_TRY(launched(c));
+    for (int r = 0; r < nrhs; ++r) {
+      double n2;
+      OV_TRY(norm2(c, OP_F64, c->o_r.c() + r * v1, V, &n2));
+      rn[r] = std::sqrt(n2);
+      res[r] = rhs_n[r] > 0 ? rn[r] / rhs_n[r] : 0.0;
+    }
+  }
+  if (!ok) {
+    double worst = 0;
+    for (double v : res) worst = std::max(worst, v);
+    ok = worst <= tol;
+  }
+  c->stats.inner_iterations = total;
+  OV_TRY(unpack_output(c, H, c->o_x.p, x, nrhs, dt));
+  if (iters) *iters = total;
+  double mx = 0;
+  for (double v : res) mx = std::max(mx, v);
+  if (true_rel_resid) *true_rel_resid = mx;
+  if (!ok) return fail(c, OV_ERR_NOT_CONVERGED, "solver stopped before reaching tol");
+  return OV_OK;
+}
+
+ov_status ov_get_stats(const ov_ctx* c, ov_stats* out) {
+  if (!c || !out) return OV_ERR_INVALID;
+  *out = c->stats;
+  return OV_OK;
+}
+
+ov_status ov_reset_stats(ov_ctx* c) {
+  if (!c) return OV_ERR_INVALID;
+  c->stats = ov_stats{};
+  return OV_OK;
+}
+
+const char* ov_last_error(const ov_ctx* c) {
+  if (!c) return g_create_error.c_str();
+  return c->err.c_str();
+}
+
+}  // extern "C"

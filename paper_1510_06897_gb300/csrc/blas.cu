@@ -1,0 +1,491 @@
+// Vector kernels: interface pack/unpack, link compression, the two deflation
+// passes of Eq. 3 (projection coefficients c_i = phi_i^dagger psi, then
+// psi_perp = psi - sum c_i phi_i together with the correction
+// sum sgn(lambda_i) c_i phi_i), and the BLAS-1 steps of CG with FP64 global
+// sums.  Every reduction runs on a fixed grid of kReduceBlocks x
+// kReduceThreads with a fixed summation order, so results are bitwise
+// reproducible run to run.
+#include "common.cuh"
+#include "internal.h"
+
+namespace ov {
+
+constexpr int kThreads = 256;
+
+static inline unsigned grid_for(int64_t n, int t = kThreads) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------------------
+// block reduction of a double2 (all threads of the block participate)
+
+__device__ __forceinline__ double2 warp_sum(double2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+// Returns the block sum in thread 0.
+__device__ __forceinline__ double2 block_sum(double2 v, double2* smem /* >= 32 */) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) smem[wid] = v;
+  __syncthreads();
+  double2 r = make_double2(0.0, 0.0);
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    r = (lane < nw) ? smem[lane] : make_double2(0.0, 0.0);
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+// arithmetic type of an operation touching storages A and B
+template <class A, class B> struct Arith { using R = float; };
+template <> struct Arith<F64, F64> { using R = double; };
+template <class B> struct Arith<F64, B> { using R = double; };
+template <class A> struct Arith<A, F64> { using R = double; };
+
+// dispatch helpers --------------------------------------------------------
+#define OV_DISPATCH1(p, T, ...)                  \
+  switch (p) {                                   \
+    case OP_F64: { using T = F64; __VA_ARGS__; } break; \
+    case OP_F32: { using T = F32; __VA_ARGS__; } break; \
+    case OP_F16: { using T = F16; __VA_ARGS__; } break; \
+    case OP_B16: { using T = B16; __VA_ARGS__; } break; \
+  }
+
+// ---------------------------------------------------------------------------
+// interface <-> internal
+
+template <class T, class IR>
+__global__ void k_pack_spinor(const IR* __restrict__ in, char* __restrict__ out, int64_t V, int64_t rhs_bytes,
+                              double scale, int g5) {
+  using R = typename Arith<T, T>::R;
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const int rhs = blockIdx.y;
+  const IR* p = in + ((int64_t)rhs * V + s) * 24;
+  Spinor<R> o;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const R sg = (g5 && k >= 6) ? R(-scale) : R(scale);
+    o.c[k] = {sg * R(p[2 * k]), sg * R(p[2 * k + 1])};
+  }
+  store_spinor_as<T, R>(out + rhs * rhs_bytes, s, V, o);
+}
+
+template <class T, class IR>
+__global__ void k_unpack_spinor(const char* __restrict__ in, IR* __restrict__ out, int64_t V, int64_t rhs_bytes,
+                                double scale) {
+  using R = typename Arith<T, T>::R;
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const int rhs = blockIdx.y;
+  Spinor<R> o;
+  load_spinor_as<T, R>(in + rhs * rhs_bytes, s, V, o);
+  IR* p = out + ((int64_t)rhs * V + s) * 24;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    p[2 * k] = IR(R(scale) * o.c[k].re);
+    p[2 * k + 1] = IR(R(scale) * o.c[k].im);
+  }
+}
+
+void launch_pack_spinor(OpPrec p, IfaceType it, const LatticeH& g, const void* in, void* out, int nrhs,
+                        double scale, int g5, cudaStream_t st) {
+  const int64_t rb = (int64_t)spinor_bytes_per_site(p) * g.V;
+  dim3 grid(grid_for(g.V), nrhs);
+  OV_DISPATCH1(p, T, {
+    if (it == IF_C128)
+      k_pack_spinor<T, double><<<grid, kThreads, 0, st>>>(static_cast<const double*>(in), static_cast<char*>(out),
+                                                          g.V, rb, scale, g5);
+    else
+      k_pack_spinor<T, float><<<grid, kThreads, 0, st>>>(static_cast<const float*>(in), static_cast<char*>(out),
+                                                         g.V, rb, scale, g5);
+  });
+}
+
+void launch_unpack_spinor(OpPrec p, IfaceType it, const LatticeH& g, const void* in, void* out, int nrhs,
+                          double scale, cudaStream_t st) {
+  const int64_t rb = (int64_t)spinor_bytes_per_site(p) * g.V;
+  dim3 grid(grid_for(g.V), nrhs);
+  OV_DISPATCH1(p, T, {
+    if (it == IF_C128)
+      k_unpack_spinor<T, double><<<grid, kThreads, 0, st>>>(static_cast<const char*>(in), static_cast<double*>(out),
+                                                            g.V, rb, scale);
+    else
+      k_unpack_spinor<T, float><<<grid, kThreads, 0, st>>>(static_cast<const char*>(in), static_cast<float*>(out),
+                                                           g.V, rb, scale);
+  });
+}
+
+template <class T>
+__global__ void k_pack_links(const double2* __restrict__ in, void* __restrict__ out, int64_t V) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const int mu = blockIdx.y;
+  const double2* u = in + ((int64_t)mu * V + s) * 9;
+  if constexpr (std::is_same<T, F64>::value) {
+    double2* q = static_cast<double2*>(out) + (int64_t)mu * 9 * V;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) q[e * V + s] = u[e];
+  } else if constexpr (std::is_same<T, F32>::value) {
+    float4* q = static_cast<float4*>(out) + (int64_t)mu * 3 * V;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      q[c * V + s] = make_float4((float)u[2 * c].x, (float)u[2 * c].y, (float)u[2 * c + 1].x, (float)u[2 * c + 1].y);
+  } else {
+    uint2* q = static_cast<uint2*>(out) + (int64_t)mu * 3 * V;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      uint2 v;
+      v.x = pack2<T>((float)u[2 * c].x, (float)u[2 * c].y);
+      v.y = pack2<T>((float)u[2 * c + 1].x, (float)u[2 * c + 1].y);
+      q[c * V + s] = v;
+    }
+  }
+}
+
+void launch_pack_links(OpPrec p, const LatticeH& g, const void* in, void* out, cudaStream_t st) {
+  dim3 grid(grid_for(g.V), 4);
+  OV_DISPATCH1(p, T, { k_pack_links<T><<<grid, kThreads, 0, st>>>(static_cast<const double2*>(in), out, g.V); });
+}
+
+// ---------------------------------------------------------------------------
+// deflation
+
+constexpr int kDeflChunk = 8;  // eigenvectors per pass over psi
+
+template <class TE, class TS>
+__global__ void __launch_bounds__(kReduceThreads) k_defl_dot(const char* __restrict__ evecs, int n_ev,
+                                                             const char* __restrict__ psi, int64_t V, int g5,
+                                                             double2* __restrict__ partial) {
+  using R = typename Arith<TE, TS>::R;
+  __shared__ double2 smem[32];
+  const int64_t evec_bytes = (int64_t)Store<TE>::bytes_per_site * V;
+  for (int i0 = 0; i0 < n_ev; i0 += kDeflChunk) {
+    double2 acc[kDeflChunk];
+#pragma unroll
+    for (int j = 0; j < kDeflChunk; ++j) acc[j] = make_double2(0.0, 0.0);
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < V; s += (int64_t)gridDim.x * blockDim.x) {
+      Spinor<R> x;
+      load_spinor_as<TS, R>(psi, s, V, x);
+      if (g5) {
+#pragma unroll
+        for (int k = 6; k < 12; ++k) x.c[k] = R(-1) * x.c[k];
+      }
+#pragma unroll
+      for (int j = 0; j < kDeflChunk; ++j) {
+        if (i0 + j < n_ev) {
+          Spinor<R> f;
+          load_spinor_as<TE, R>(evecs + (i0 + j) * evec_bytes, s, V, f);
+          cplx<R> d = {R(0), R(0)};
+#pragma unroll
+          for (int k = 0; k < 12; ++k) d = d + cmulc(f.c[k], x.c[k]);
+          acc[j].x += (double)d.re;
+          acc[j].y += (double)d.im;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kDeflChunk; ++j) {
+      if (i0 + j < n_ev) {
+        double2 r = block_sum(acc[j], smem);
+        if (threadIdx.x == 0) partial[(int64_t)(i0 + j) * gridDim.x + blockIdx.x] = r;
+      }
+    }
+  }
+}
+
+void launch_defl_dot(OpPrec pv, const LatticeH& g, const void* evecs, int n_ev, const void* psi, int g5,
+                     double2* partial, cudaStream_t st) {
+  if (n_ev <= 0) return;
+  OV_DISPATCH1(pv, T, {
+    k_defl_dot<T, T><<<kReduceBlocks, kReduceThreads, 0, st>>>(static_cast<const char*>(evecs), n_ev,
+                                                               static_cast<const char*>(psi), g.V, g5, partial);
+  });
+}
+
+__global__ void k_reduce_partials(const double2* __restrict__ partial, int nblk, double2* __restrict__ out) {
+  __shared__ double2 smem[32];
+  const int i = blockIdx.x;
+  double2 v = make_double2(0.0, 0.0);
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+    const double2 p = partial[(int64_t)i * nblk + b];
+    v.x += p.x;
+    v.y += p.y;
+  }
+  v = block_sum(v, smem);
+  if (threadIdx.x == 0) out[i] = v;
+}
+
+void launch_reduce_partials(const double2* partial, int n, int nblk, double2* out, cudaStream_t st) {
+  if (n <= 0) return;
+  k_reduce_partials<<<n, 256, 0, st>>>(partial, nblk, out);
+}
+
+// TV: storage of phi_i, psi and d; TP: storage of psi_perp.
+template <class TV, class TP>
+__global__ void k_defl_combine(const char* __restrict__ evecs, int n_ev, const double2* __restrict__ c,
+                               const double* __restrict__ sgn, const char* __restrict__ psi, int64_t V, int g5,
+                               double scale, char* __restrict__ psi_perp, char* __restrict__ d) {
+  using R = typename Arith<TV, TV>::R;
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const int64_t evec_bytes = (int64_t)Store<TV>::bytes_per_site * V;
+  Spinor<R> x, corr;
+  load_spinor_as<TV, R>(psi, s, V, x);
+  if (g5) {
+#pragma unroll
+    for (int k = 6; k < 12; ++k) x.c[k] = R(-1) * x.c[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) corr.c[k] = {R(0), R(0)};
+  for (int i = 0; i < n_ev; ++i) {
+    Spinor<R> f;
+    load_spinor_as<TV, R>(evecs + i * evec_bytes, s, V, f);
+    const cplx<R> ci = {R(c[i].x), R(c[i].y)};
+    const R si = R(sgn[i]);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const cplx<R> t = cmul(ci, f.c[k]);
+      x.c[k] = x.c[k] - t;
+      corr.c[k] = corr.c[k] + si * t;
+    }
+  }
+  const R sc = R(scale);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    x.c[k] = sc * x.c[k];
+    corr.c[k] = sc * corr.c[k];
+  }
+  store_spinor_as<TP, R>(psi_perp, s, V, x);
+  if (d != nullptr) store_spinor_as<TV, R>(d, s, V, corr);
+}
+
+void launch_defl_combine(OpPrec pv, OpPrec pp, const LatticeH& g, const void* evecs, int n_ev, const double2* c,
+                         const double* sgn, const void* psi, int g5, double scale, void* psi_perp, void* d,
+                         cudaStream_t st) {
+  const char* e = static_cast<const char*>(evecs);
+  const char* x = static_cast<const char*>(psi);
+  char* pp_ = static_cast<char*>(psi_perp);
+  char* dd = static_cast<char*>(d);
+  const unsigned gr = grid_for(g.V);
+  if (pv == OP_F64) {
+    k_defl_combine<F64, F64><<<gr, kThreads, 0, st>>>(e, n_ev, c, sgn, x, g.V, g5, scale, pp_, dd);
+  } else {
+    OV_DISPATCH1(pp, TP, {
+      k_defl_combine<F32, TP><<<gr, kThreads, 0, st>>>(e, n_ev, c, sgn, x, g.V, g5, scale, pp_, dd);
+    });
+  }
+}
+
+// ---------------------------------------------------------------------------
+// BLAS-1 on same-storage vectors, treated as flat arrays of complex numbers
+// (layout-agnostic: all operands share the layout).  A "unit" is one storage
+// chunk; unit_complex complex numbers per unit.
+
+template <class T> struct Unit;
+template <> struct Unit<F64> {
+  using U = double2;
+  static constexpr int n = 1;
+  __device__ static void load(const U& u, cplx<double>* c) { c[0] = {u.x, u.y}; }
+  __device__ static U store(const cplx<double>* c) { return make_double2(c[0].re, c[0].im); }
+};
+template <> struct Unit<F32> {
+  using U = float4;
+  static constexpr int n = 2;
+  __device__ static void load(const U& u, cplx<float>* c) {
+    c[0] = {u.x, u.y};
+    c[1] = {u.z, u.w};
+  }
+  __device__ static U store(const cplx<float>* c) { return make_float4(c[0].re, c[0].im, c[1].re, c[1].im); }
+};
+template <class T> struct Unit16 {
+  using U = uint4;
+  static constexpr int n = 4;
+  __device__ static void load(const U& u, cplx<float>* c) {
+    float2 a = unpack2<T>(u.x), b = unpack2<T>(u.y), d = unpack2<T>(u.z), e = unpack2<T>(u.w);
+    c[0] = {a.x, a.y};
+    c[1] = {b.x, b.y};
+    c[2] = {d.x, d.y};
+    c[3] = {e.x, e.y};
+  }
+  __device__ static U store(const cplx<float>* c) {
+    U u;
+    u.x = pack2<T>(c[0].re, c[0].im);
+    u.y = pack2<T>(c[1].re, c[1].im);
+    u.z = pack2<T>(c[2].re, c[2].im);
+    u.w = pack2<T>(c[3].re, c[3].im);
+    return u;
+  }
+};
+template <> struct Unit<F16> : Unit16<F16> {};
+template <> struct Unit<B16> : Unit16<B16> {};
+
+template <class T>
+static inline int64_t n_units(int64_t V, int nrhs) {
+  return V * nrhs * 12 / Unit<T>::n;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kReduceThreads) k_dot_partial(const typename Unit<T>::U* __restrict__ a,
+                                                                const typename Unit<T>::U* __restrict__ b, int64_t n,
+                                                                double2* __restrict__ partial, int norm_only) {
+  using R = typename Arith<T, T>::R;
+  constexpr int m = Unit<T>::n;
+  __shared__ double2 smem[32];
+  double2 acc = make_double2(0.0, 0.0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    cplx<R> x[m], y[m];
+    Unit<T>::load(a[i], x);
+    if (norm_only) {
+      R t = R(0);
+#pragma unroll
+      for (int k = 0; k < m; ++k) t += x[k].re * x[k].re + x[k].im * x[k].im;
+      acc.x += (double)t;
+    } else {
+      Unit<T>::load(b[i], y);
+      cplx<R> t = {R(0), R(0)};
+#pragma unroll
+      for (int k = 0; k < m; ++k) t = t + cmulc(x[k], y[k]);
+      acc.x += (double)t.re;
+      acc.y += (double)t.im;
+    }
+  }
+  acc = block_sum(acc, smem);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+void launch_dot_partial(OpPrec p, const void* a, const void* b, int64_t V, int nrhs, double2* partial,
+                        cudaStream_t st) {
+  OV_DISPATCH1(p, T, {
+    using U = typename Unit<T>::U;
+    k_dot_partial<T><<<kReduceBlocks, kReduceThreads, 0, st>>>(static_cast<const U*>(a), static_cast<const U*>(b),
+                                                               n_units<T>(V, nrhs), partial, 0);
+  });
+}
+
+void launch_norm2_partial(OpPrec p, const void* a, int64_t V, int nrhs, double2* partial, cudaStream_t st) {
+  OV_DISPATCH1(p, T, {
+    using U = typename Unit<T>::U;
+    k_dot_partial<T><<<kReduceBlocks, kReduceThreads, 0, st>>>(static_cast<const U*>(a), static_cast<const U*>(a),
+                                                               n_units<T>(V, nrhs), partial, 1);
+  });
+}
+
+template <class T>
+__global__ void __launch_bounds__(kReduceThreads) k_cg_update_xr(typename Unit<T>::U* __restrict__ x,
+                                                                 typename Unit<T>::U* __restrict__ r,
+                                                                 const typename Unit<T>::U* __restrict__ p,
+                                                                 const typename Unit<T>::U* __restrict__ q,
+                                                                 double alpha, int64_t n,
+                                                                 double2* __restrict__ partial) {
+  using R = typename Arith<T, T>::R;
+  constexpr int m = Unit<T>::n;
+  __shared__ double2 smem[32];
+  const R al = R(alpha);
+  double2 acc = make_double2(0.0, 0.0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    cplx<R> xv[m], rv[m], pv[m], qv[m];
+    Unit<T>::load(x[i], xv);
+    Unit<T>::load(r[i], rv);
+    Unit<T>::load(p[i], pv);
+    Unit<T>::load(q[i], qv);
+    R t = R(0);
+#pragma unroll
+    for (int k = 0; k < m; ++k) {
+      xv[k] = xv[k] + al * pv[k];
+      rv[k] = rv[k] - al * qv[k];
+      t += rv[k].re * rv[k].re + rv[k].im * rv[k].im;
+    }
+    x[i] = Unit<T>::store(xv);
+    r[i] = Unit<T>::store(rv);
+    acc.x += (double)t;
+  }
+  acc = block_sum(acc, smem);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+void launch_cg_update_xr(OpPrec p, void* x, void* r, const void* pv, const void* q, double alpha, int64_t V, int nrhs,
+                         double2* partial, cudaStream_t st) {
+  OV_DISPATCH1(p, T, {
+    using U = typename Unit<T>::U;
+    k_cg_update_xr<T><<<kReduceBlocks, kReduceThreads, 0, st>>>(static_cast<U*>(x), static_cast<U*>(r),
+                                                                static_cast<const U*>(pv), static_cast<const U*>(q),
+                                                                alpha, n_units<T>(V, nrhs), partial);
+  });
+}
+
+template <class T>
+__global__ void k_axpby(double a, const typename Unit<T>::U* x, double b, const typename Unit<T>::U* y,
+                        typename Unit<T>::U* out, int64_t n) {
+  using R = typename Arith<T, T>::R;
+  constexpr int m = Unit<T>::n;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  cplx<R> xv[m], yv[m];
+  Unit<T>::load(x[i], xv);
+  if (y != nullptr) {
+    Unit<T>::load(y[i], yv);
+#pragma unroll
+    for (int k = 0; k < m; ++k) xv[k] = R(a) * xv[k] + R(b) * yv[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < m; ++k) xv[k] = R(a) * xv[k];
+  }
+  out[i] = Unit<T>::store(xv);
+}
+
+void launch_axpby(OpPrec p, double a, const void* x, double b, const void* y, void* out, int64_t V, int nrhs,
+                  cudaStream_t st) {
+  OV_DISPATCH1(p, T, {
+    using U = typename Unit<T>::U;
+    const int64_t n = n_units<T>(V, nrhs);
+    k_axpby<T><<<grid_for(n), kThreads, 0, st>>>(a, static_cast<const U*>(x), b, static_cast<const U*>(y),
+                                                 static_cast<U*>(out), n);
+  });
+}
+
+void launch_cg_update_p(OpPrec p, void* pv, const void* r, double beta, int64_t V, int nrhs, cudaStream_t st) {
+  launch_axpby(p, 1.0, r, beta, pv, pv, V, nrhs, st);
+}
+
+// per-site conversion between storages (layouts differ between storages)
+template <class TI, class TO>
+__global__ void k_convert(const char* __restrict__ in, char* out, int64_t V, int64_t in_rb, int64_t out_rb,
+                          double scale, int accumulate) {
+  using R = typename Arith<TI, TO>::R;
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const int rhs = blockIdx.y;
+  Spinor<R> x;
+  load_spinor_as<TI, R>(in + rhs * in_rb, s, V, x);
+  const R sc = R(scale);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) x.c[k] = sc * x.c[k];
+  if (accumulate) {
+    Spinor<R> y;
+    load_spinor_as<TO, R>(out + rhs * out_rb, s, V, y);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) x.c[k] = x.c[k] + y.c[k];
+  }
+  store_spinor_as<TO, R>(out + rhs * out_rb, s, V, x);
+}
+
+void launch_convert(OpPrec pi, OpPrec po, const void* in, void* out, int64_t V, int nrhs, double scale,
+                    int accumulate, cudaStream_t st) {
+  const int64_t irb = (int64_t)spinor_bytes_per_site(pi) * V, orb = (int64_t)spinor_bytes_per_site(po) * V;
+  dim3 grid(grid_for(V), nrhs);
+  OV_DISPATCH1(pi, TI, {
+    OV_DISPATCH1(po, TO, {
+      k_convert<TI, TO><<<grid, kThreads, 0, st>>>(static_cast<const char*>(in), static_cast<char*>(out), V, irb,
+                                                   orb, scale, accumulate);
+    });
+  });
+}
+
+}  // namespace ov

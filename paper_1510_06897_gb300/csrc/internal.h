@@ -1,0 +1,104 @@
+// Host-side declarations shared by the translation units of the library.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ov {
+
+// Storage precision of an operator instance (links and the spinors of its
+// recurrence are stored in this type; arithmetic is FP64 for OP_F64 and FP32
+// otherwise).
+enum OpPrec { OP_F64 = 0, OP_F32 = 1, OP_F16 = 2, OP_B16 = 3 };
+
+inline int spinor_bytes_per_site(OpPrec p) {
+  return p == OP_F64 ? 192 : p == OP_F32 ? 96 : 48;
+}
+// bytes of one direction's link at one site as stored
+inline int link_bytes_per_site_dir(OpPrec p) {
+  return p == OP_F64 ? 144 : p == OP_F32 ? 48 : 24;
+}
+
+struct LatticeH {
+  int L[4];
+  int64_t V;
+  int antiperiodic_t;
+};
+
+// Fused epilogue of one stencil application:
+//   r   = D_W x                      (wilson = 1)
+//       = gamma5 (D_W - m_w) x = K x (wilson = 0)
+//   out = c0 * y + G( s1 * r + sum_j w[j] * v[j] + wz * z ),  G = gamma5 if g5_out else 1
+// Null v[j] / z / y are skipped.  The stencil input x and v[j] are in the
+// operator's storage p; z, y and out are in out_prec (p itself, or FP32 for a
+// 16-bit operator whose results are assembled in FP32).
+struct EpiArgs {
+  int wilson = 0;
+  double m_w = 1.5;
+  int g5_out = 0;
+  double s1 = 1.0;
+  const void* v[3] = {nullptr, nullptr, nullptr};
+  double w[3] = {0.0, 0.0, 0.0};
+  const void* z = nullptr;
+  double wz = 0.0;
+  const void* y = nullptr;
+  double c0 = 0.0;
+};
+
+void launch_dslash(OpPrec p, OpPrec out_prec, const LatticeH& g, const void* links, const void* in, void* out,
+                   const EpiArgs& e, int nrhs, cudaStream_t st);
+
+// ---- vector kernels (blas.cu) ---------------------------------------------
+// Interface formats: complex128 / complex64 AoS [nrhs][V][4][3].
+enum IfaceType { IF_C128 = 0, IF_C64 = 1 };
+
+// internal <- interface, out = scale * (g5 ? gamma5 : 1) in
+void launch_pack_spinor(OpPrec p, IfaceType it, const LatticeH& g, const void* in, void* out, int nrhs,
+                        double scale, int g5, cudaStream_t st);
+// interface <- internal
+void launch_unpack_spinor(OpPrec p, IfaceType it, const LatticeH& g, const void* in, void* out, int nrhs,
+                          double scale, cudaStream_t st);
+// links complex128 [4][V][3][3] -> internal storage
+void launch_pack_links(OpPrec p, const LatticeH& g, const void* in, void* out, cudaStream_t st);
+
+// Number of blocks every reduction kernel uses (fixed, so that results are
+// bitwise reproducible).
+constexpr int kReduceBlocks = 608;
+constexpr int kReduceThreads = 256;
+
+// Deflation, step 1: partial[i][blk] = sum over the block's sites of
+// conj(phi_i) . ((g5 ? gamma5 : 1) psi), i < n_ev; complex, per-site products
+// in the storage's arithmetic, sums over sites in FP64.  phi (n_ev vectors
+// of V sites, back to back) and psi in storage pv (FP64 or FP32).
+void launch_defl_dot(OpPrec pv, const LatticeH& g, const void* evecs, int n_ev, const void* psi,
+                     int g5, double2* partial, cudaStream_t st);
+// sum partial[i][0..nblk) in a fixed order -> out[i]
+void launch_reduce_partials(const double2* partial, int n, int nblk, double2* out, cudaStream_t st);
+// Deflation, step 2 (and conversion into the recurrence's storage):
+//   psi_perp = scale * (G psi - sum_i c_i phi_i),   d = scale * sum_i sgn_i c_i phi_i
+// (d skipped when null; G = gamma5 if g5).
+// phi, psi and d are in storage pv (FP64 or FP32), psi_perp in pp (the
+// operator's recurrence storage).
+void launch_defl_combine(OpPrec pv, OpPrec pp, const LatticeH& g, const void* evecs, int n_ev,
+                         const double2* c, const double* sgn, const void* psi, int g5, double scale,
+                         void* psi_perp, void* d, cudaStream_t st);
+
+// BLAS-1 on internal spinors of storage p: nrhs fields of V sites each,
+// stored back to back.  Reductions leave one double2 per block in partial[]
+// (complex dot: re/im; norm: .x), to be summed by launch_reduce_partials.
+void launch_dot_partial(OpPrec p, const void* a, const void* b, int64_t V, int nrhs, double2* partial,
+                        cudaStream_t st);
+void launch_norm2_partial(OpPrec p, const void* a, int64_t V, int nrhs, double2* partial, cudaStream_t st);
+// x += alpha p ; r -= alpha q ; partial |r|^2
+void launch_cg_update_xr(OpPrec p, void* x, void* r, const void* pv, const void* q, double alpha, int64_t V,
+                         int nrhs, double2* partial, cudaStream_t st);
+// p = r + beta p
+void launch_cg_update_p(OpPrec p, void* pv, const void* r, double beta, int64_t V, int nrhs, cudaStream_t st);
+// out = a*x + b*y (out may alias x or y; y may be null => out = a*x)
+void launch_axpby(OpPrec p, double a, const void* x, double b, const void* y, void* out, int64_t V, int nrhs,
+                  cudaStream_t st);
+// out (storage po) = scale * in (storage pi)            (accumulate = 0)
+// out (storage po) = out + scale * in (storage pi)      (accumulate = 1)
+void launch_convert(OpPrec pi, OpPrec po, const void* in, void* out, int64_t V, int nrhs, double scale,
+                    int accumulate, cudaStream_t st);
+
+}  // namespace ov

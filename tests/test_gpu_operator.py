@@ -1,0 +1,155 @@
+"""GPU parity of D_W, K, sign(K), D[mu] and D[mu]^dagger against the FP64 oracle,
+through the C ABI (paper_1510_06897_gb300.binding).
+
+Tolerances (relative L2 error over the whole field, all RHS):
+  fp64  1e-12   (the FP64 path must reproduce the oracle to rounding)
+  fp32  1e-5    (FP32 storage and arithmetic, FP64 global sums)
+  fp16  / bf16: storage rounding u = 2^-11 / 2^-8 of links and vectors bounds a
+        single stencil application by a few u; the recurrence adds a few u per
+        term in a random walk, hence the looser sign/overlap bounds below.
+"""
+import numpy as np
+import pytest
+
+from oracle import chebyshev, overlap, wilson
+from paper_1510_06897_gb300 import inputs
+from paper_1510_06897_gb300.binding import Ctx, OverlapError
+from tests.gpu_util import dev, host, need_gpu, rel, torch
+from tests.oracle_fixtures import field_shape, small_problem
+
+pytestmark = pytest.mark.gpu
+
+STENCIL_TOL = {"fp64": 1e-13, "fp32": 1e-6, "fp16": 2e-3, "bf16": 1.5e-2}
+SIGN_TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp16": 1e-2, "bf16": 6e-2}
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("dims,antiperiodic", [((4, 4, 4, 4), False), ((6, 4, 2, 8), True), ((8, 8, 8, 8), False),
+                                              ((16, 16, 16, 32), True)])
+def test_wilson_and_kernel(prec, dims, antiperiodic):
+    links = inputs.gauge_links(dims, seed=4001)
+    psi = inputs.gaussian_source(dims, seed=4002, nrhs=2)
+    with Ctx(dims, dev(links), prec, antiperiodic_t=antiperiodic) as c:
+        got_w = host(c.wilson(dev(psi)))
+        got_k = host(c.kernel(dev(psi)))
+    want_w = np.stack([wilson.wilson(links, p, antiperiodic) for p in psi])
+    want_k = np.stack([wilson.kernel_k(links, p, antiperiodic_t=antiperiodic) for p in psi])
+    assert rel(got_w, want_w) < STENCIL_TOL[prec]
+    assert rel(got_k, want_k) < STENCIL_TOL[prec]
+
+
+def test_wilson_complex64_and_host_pointers():
+    dims = (4, 4, 4, 8)
+    links = inputs.gauge_links(dims, seed=4011)
+    psi = inputs.gaussian_source(dims, seed=4012)
+    want = wilson.wilson(links, psi[0])[None]
+    with Ctx(dims, links, "fp64") as c:                     # links from host memory
+        out_host = np.empty_like(psi)
+        from paper_1510_06897_gb300.binding import ov_wilson
+        ov_wilson(c.handle, psi, out_host, 1)               # host in, host out
+        assert rel(out_host, want) < 1e-13
+        got64 = host(c.wilson(dev(psi.astype(np.complex64))))
+        assert got64.dtype == np.complex64
+        assert rel(got64, want) < 1e-6
+
+
+def _sign_setup(prob, order):
+    c = chebyshev.coefficients(order, prob["a"], prob["b"])
+    return overlap.SignConfig(c, prob["a"], prob["b"], prob["evals"], prob["evecs"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
+def test_sign_overlap_4x4(prec):
+    """4^4, 8 dense eigenpairs deflated, order 64 on [|lambda_9|, lambda_max]."""
+    prob = small_problem()
+    cfg = _sign_setup(prob, 64)
+    psi = inputs.gaussian_source(prob["dims"], seed=4101, nrhs=2)
+    mu = 0.05
+    want_s = np.stack([overlap.sign_apply(prob["links"], p, cfg) for p in psi])
+    want_d = np.stack([overlap.overlap(prob["links"], p, mu, cfg) for p in psi])
+    want_dd = np.stack([overlap.overlap_dag(prob["links"], p, mu, cfg) for p in psi])
+    with Ctx(prob["dims"], dev(prob["links"]), prec) as c:
+        c.sign_config(64, prob["a"], prob["b"], prob["evals"], dev(prob["evecs"]))
+        got_s = host(c.sign(dev(psi)))
+        got_d = host(c.overlap(dev(psi), mu))
+        got_dd = host(c.overlap(dev(psi), mu, dagger=True))
+    print(prec, rel(got_s, want_s), rel(got_d, want_d), rel(got_dd, want_dd))
+    assert rel(got_s, want_s) < SIGN_TOL[prec]
+    assert rel(got_d, want_d) < SIGN_TOL[prec]
+    assert rel(got_dd, want_dd) < SIGN_TOL[prec]
+
+
+@pytest.mark.parametrize("order", [1, 2, 7])
+def test_sign_low_orders_undeflated(order):
+    """Degenerate recurrence lengths (N = 1, 2) and no deflation."""
+    dims = (4, 2, 2, 4)
+    links = inputs.gauge_links(dims, seed=4201)
+    psi = inputs.gaussian_source(dims, seed=4202)
+    a, b = 0.3, 6.6
+    cfg = overlap.SignConfig(chebyshev.coefficients(order, a, b), a, b)
+    want = overlap.sign_apply(links, psi[0], cfg)[None]
+    with Ctx(dims, dev(links), "fp64") as c:
+        c.sign_config(order, a, b)
+        got = host(c.sign(dev(psi)))
+    assert rel(got, want) < 1e-13
+
+
+def test_sign_ragged_and_asymmetric():
+    """Lattice whose volume is not a multiple of the block size, antiperiodic t,
+    3 RHS, deflation with eigenpairs from the dense spectrum."""
+    prob = small_problem((3, 2, 5, 4), seed=4301, n_ev=6, antiperiodic=True)
+    cfg = _sign_setup(prob, 20)
+    psi = inputs.gaussian_source(prob["dims"], seed=4302, nrhs=3)
+    want = np.stack([overlap.sign_apply(prob["links"], p, cfg, antiperiodic_t=True) for p in psi])
+    with Ctx(prob["dims"], dev(prob["links"]), "fp64", antiperiodic_t=True) as c:
+        c.sign_config(20, prob["a"], prob["b"], prob["evals"], dev(prob["evecs"]))
+        got = host(c.sign(dev(psi)))
+    assert rel(got, want) < 1e-12
+
+
+def test_free_field_sign_full_size():
+    """24^3 x 48, U = 1, order 256: P(K) psi_p = f_N(A^2 + s^2) K(p) psi_p on a
+    plane wave (closed form, no oracle run needed at this volume)."""
+    dims = (24, 24, 24, 48)
+    n = (1, 5, 3, 7)
+    rng = np.random.default_rng(4401)
+    u = rng.standard_normal((4, 3)) + 1j * rng.standard_normal((4, 3))
+    p = [2 * np.pi * n[i] / dims[i] for i in range(4)]
+    t, z, y, x = np.meshgrid(*(np.arange(dims[3 - i]) for i in range(4)), indexing="ij")
+    psi = (np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))[..., None, None] * u)[None]
+    a, b, order = 0.45, 6.5, 256
+    c = chebyshev.coefficients(order, a, b)
+    big_a = sum(1 - np.cos(pm) for pm in p) - wilson.M_W
+    s2 = sum(np.sin(pm) ** 2 for pm in p)
+    kp = wilson.GAMMA5 @ (big_a * np.eye(4) + 1j * sum(wilson.GAMMA[mu] * np.sin(p[mu]) for mu in range(4)))
+    fval = chebyshev.f_scalar(c, a, b, big_a ** 2 + s2)
+    want = fval * np.einsum("st,...ta->...sa", kp, psi)
+    links = inputs.unit_links(dims)
+    for prec, tol in (("fp64", 1e-12), ("fp32", 2e-5)):
+        with Ctx(dims, dev(links), prec) as cx:
+            cx.sign_config(order, a, b)
+            got = host(cx.sign(dev(psi)))
+        assert rel(got, want) < tol, prec
+
+
+def test_errors_and_state():
+    dims = (4, 4, 4, 4)
+    links = inputs.gauge_links(dims, seed=4501)
+    psi = dev(inputs.gaussian_source(dims, seed=4502))
+    with Ctx(dims, dev(links), "fp32") as c:
+        with pytest.raises(OverlapError) as e:
+            c.sign(psi)
+        assert e.value.status == 5  # OV_ERR_STATE
+        with pytest.raises(OverlapError) as e:
+            c.sign_config(0, 0.5, 6.5)
+        assert e.value.status == 1
+        with pytest.raises(OverlapError) as e:
+            c.sign_config(8, 6.5, 0.5)
+        assert e.value.status == 1
+        c.sign_config(8, 0.5, 6.5)
+        assert np.all(np.isfinite(host(c.sign(psi))))
