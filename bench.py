@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Benchmark of the overlap hot path on one GB300 (or N independent replicas).
+
+Workload (the 24^3 x 48 lattice the headline metric is quoted on):
+  links U = exp(i 0.3 H) seeded (synthetic stand-in for the paper's smeared
+  ensembles), 40 deflated eigenpairs of K from ov_eigs, Chebyshev order 256 on
+  [|lambda_41|, lambda_max], Gaussian source.  One step = one sign(K) psi
+  application through the C ABI (deflation projection, 2N+1 fused stencil
+  launches, deflation correction), inputs resident in HBM; the working set
+  (links, eigenvectors, recurrence vectors: several GB) is far larger than L2.
+
+Also reported: the stencil's achieved HBM bandwidth (algorithmic bytes over
+its CUDA-event-timed launches inside the timed region), the same metric end
+to end through host buffers, sign(K) applies/s in every precision, and the
+time to a 1e-10 solve of D^dagger D (mixed precision; FP64 with --fp64-solve).
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sign(K)ψ applies/s & dslash HBM GB/s at 24^3×48, mixed vs FP64 at 1e-10"
+DIMS = (24, 24, 24, 48)
+ORDER = 256
+N_EV = 40
+MU = 0.02
+SEED_LINKS = 1003
+SEED_SRC = 2003
+FALLBACK_HBM_GBS = 6800.0
+
+# bytes per site of one stored object, per precision
+LINK_B = {"fp64": 4 * 144, "fp32": 4 * 48, "fp16": 4 * 24, "bf16": 4 * 24}
+SPIN_B = {"fp64": 192, "fp32": 96, "fp16": 48, "bf16": 48}
+VEC_B = {"fp64": 192, "fp32": 96, "fp16": 96, "bf16": 96}
+
+
+def stencil_bytes_per_apply(prec, order, n_ev, vol):
+    """Algorithmic HBM bytes of the 2N+1 stencil launches of one sign(K) apply:
+    every link once, every vector read or written once per launch."""
+    l, s, v = LINK_B[prec], SPIN_B[prec], VEC_B[prec]
+    k_steps = order * (l + 2 * s)                          # t = K b_{k+1}
+    clenshaw = (l + 3 * s) + (order - 1) * (l + 5 * s)     # first step reads psi_perp once
+    final = l + s + v + (v if n_ev else 0)                 # K h (+ d) -> FP vector out
+    return vol * (k_steps + clenshaw + final)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def ncu_traffic(prec):
+    """DRAM bytes per site per stencil launch from the committed ncu summary,
+    if it was taken on the current stencil source (else None)."""
+    src = os.path.join(ROOT, "paper_1510_06897_gb300", "csrc", "dslash.cu")
+    path = os.path.join(ROOT, "profiles", "dslash_24x24x24x48.md")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        text = open(path).read()
+    except OSError:
+        return None
+    if f"source_sha256_16: {sha}" not in text:
+        return None
+    for line in text.splitlines():
+        if line.startswith(f"traffic_bytes_per_site_{prec}:"):
+            return float(line.split(":")[1])
+    return None
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(links, evecs_host, evals, a, b, order, sample_terms=2, sample_evecs=4):
+    """The FP64 oracle timed on the host: sample_terms Chebyshev terms and the
+    deflation with sample_evecs eigenvectors, extrapolated to one full sign(K)
+    apply (order terms, one final K, 40 eigenvectors)."""
+    import oracle
+    from oracle import chebyshev, overlap, wilson
+    from paper_1510_06897_gb300 import inputs
+
+    psi = inputs.gaussian_source(DIMS, seed=SEED_SRC)[0]
+    c = chebyshev.coefficients(sample_terms, a, b)
+
+    def kop(w):
+        return wilson.kernel_k(links, w)
+
+    t0 = time.perf_counter()
+    chebyshev.apply_fn(kop, c, a, b, psi)
+    t_terms = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    kop(psi)
+    t_k = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    cfg = overlap.SignConfig(c, a, b, evals[:sample_evecs], evecs_host[:sample_evecs])
+    coeffs = overlap.project(cfg.evecs, psi)
+    perp = psi.copy()
+    for i in range(sample_evecs):
+        perp = perp - coeffs[i] * cfg.evecs[i]
+    t_defl = time.perf_counter() - t0
+    per_apply = t_terms / sample_terms * order + t_k + 2 * t_defl * N_EV / sample_evecs
+    return {"value": 1.0 / per_apply, "unit": "applies/s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 NumPy oracle on 24^3x48: {sample_terms} Chebyshev terms ({2 * sample_terms} K), "
+                       f"1 K, projection onto {sample_evecs} eigenvectors; extrapolated to {order} terms + "
+                       f"{N_EV}-vector deflation ({per_apply:.1f} s per apply)"),
+            "sample_seconds": t_terms + t_k + t_defl}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle, each step a bounded sample of the workload."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from oracle import chebyshev, wilson
+    from paper_1510_06897_gb300 import inputs
+
+    links = inputs.gauge_links(DIMS, seed=SEED_LINKS)
+    psi = inputs.gaussian_source(DIMS, seed=SEED_SRC)[0]
+    a, b = 0.45, 6.5
+    c = chebyshev.coefficients(1, a, b)
+
+    def kop(w):
+        return wilson.kernel_k(links, w)
+
+    def step():  # one Chebyshev term (2 K applications + the recurrence algebra)
+        chebyshev.apply_fn(kop, c, a, b, psi)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    per_term = (time.perf_counter() - t0) / args.steps
+    per_apply = per_term * ORDER
+    value = 1.0 / per_apply
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_term * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "24^3x48 sign(K) psi, Chebyshev order 256 (oracle: one term per step, "
+                                   "extrapolated x256; deflation not included)", "lattice": "24x24x24x48"},
+            "cpu_baseline": {"value": value, "unit": "applies/s", "kind": "oracle", "cores": 1,
+                             "sample": "one Chebyshev term (2 K applications) of the FP64 NumPy oracle per step"},
+            "e2e": {"value": value, "unit": "applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp16", choices=["fp16", "bf16", "fp32", "fp64"])
+    ap.add_argument("--no-extras", action="store_true", help="headline only")
+    ap.add_argument("--fp64-solve", action="store_true", help="also time the plain FP64 solve (minutes)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    from paper_1510_06897_gb300 import inputs
+    from paper_1510_06897_gb300.binding import (Ctx, ov_eigs, ov_get_stats, ov_reset_stats, ov_set_profiling,
+                                                ov_sign_apply, ov_solve)
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    vol = inputs.volume(DIMS)
+    t_setup = time.perf_counter()
+    links = inputs.gauge_links(DIMS, seed=SEED_LINKS)
+    links_d = torch.from_numpy(links).cuda()
+    fshape = (DIMS[3], DIMS[2], DIMS[1], DIMS[0], 4, 3)
+
+    # S0 setup (not timed): eigenpairs of K from an FP32 context
+    evecs = torch.zeros((N_EV + 1,) + fshape, dtype=torch.complex128, device="cuda")
+    t_eigs = time.perf_counter()
+    with Ctx(DIMS, links_d, "fp32") as c32:
+        evals, lmax = ov_eigs(c32.handle, N_EV + 1, 2e-5, 300, evecs)
+    t_eigs = time.perf_counter() - t_eigs
+    a, b = float(abs(evals[N_EV])), float(lmax)
+    evals40, evecs40 = evals[:N_EV].copy(), evecs[:N_EV].contiguous()
+    del evecs
+
+    psi = torch.from_numpy(inputs.gaussian_source(DIMS, seed=SEED_SRC)).cuda()
+    out = torch.empty_like(psi)
+    ctx = Ctx(DIMS, links_d, args.prec)
+    ctx.sign_config(ORDER, a, b, evals40, evecs40)
+    setup_s = time.perf_counter() - t_setup
+
+    for _ in range(args.warmup):
+        ov_sign_apply(ctx.handle, psi, out, 1)
+    torch.cuda.synchronize()
+    ov_reset_stats(ctx.handle)
+    ov_set_profiling(ctx.handle, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ov_sign_apply(ctx.handle, psi, out, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    ov_set_profiling(ctx.handle, False)
+    elapsed_ms = e0.elapsed_time(e1)
+    st = ov_get_stats(ctx.handle)
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = world * args.steps / (elapsed_ms * 1e-3)
+
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    bytes_apply = stencil_bytes_per_apply(args.prec, ORDER, N_EV, vol)
+    launches_per_apply = 2 * ORDER + 1
+    dslash_ms_avg = st["dslash_ms"] / max(1, st["dslash_timed"])
+    achieved = (bytes_apply / launches_per_apply) / (dslash_ms_avg * 1e-3) / 1e9
+    traffic_site = ncu_traffic(args.prec)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": (traffic_site * vol if traffic_site is not None else None),
+                "kernel": f"k_dslash ({args.prec} storage), average over the 2N+1 launches of a sign apply",
+                "algorithmic_bytes_per_launch": bytes_apply / launches_per_apply,
+                "avg_launch_us": dslash_ms_avg * 1e3, "peak_source": f"hbm_gbs of {peak_kind}",
+                "stencil_share_of_step": st["dslash_ms"] / elapsed_ms if world == 1 else None}
+
+    # end to end through the C ABI with host (pinned) buffers
+    psi_h = psi.cpu().pin_memory()
+    out_h = torch.empty_like(psi_h).pin_memory()
+    n_e2e = max(3, min(args.steps, 10))
+    ov_sign_apply(ctx.handle, psi_h, out_h, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        ov_sign_apply(ctx.handle, psi_h, out_h, 1)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    iface = vol * 12 * 16
+    e2e = {"value": world / e2e_s, "unit": "applies/s", "h2d_bytes_per_step": iface, "d2h_bytes_per_step": iface}
+
+    line = {"metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.prec != "fp64" else "f64",
+            "data": "synthetic (seeded exp(i 0.3 H) links, Gaussian source)",
+            "config": {"workload": f"24^3x48 sign(K) psi, Chebyshev order {ORDER}, {N_EV} deflated eigenpairs, "
+                                   f"{args.prec} storage",
+                       "lattice": "24x24x24x48", "order": ORDER, "n_ev": N_EV, "storage": args.prec,
+                       "interval": [a, b], "l2": "inputs larger than L2 (links + eigenvectors + vectors, GBs)",
+                       "parallelism": "replicas" if world > 1 else "1 GPU", "setup_s": setup_s,
+                       "eigs_s": t_eigs},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": st["kernel_launches"], "clocks": clk}
+
+    if rank == 0 and not args.no_extras:
+        line["extras"] = extras(args, ctx, links_d, a, b, evals40, evecs40, psi, vol)
+    ctx.close()
+    if rank == 0 and world == 1 and not args.no_cpu:
+        evh = evecs40[:4].cpu().numpy()
+        line["cpu_baseline"] = cpu_baseline(links, evh, evals40, a, b, ORDER)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def extras(args, ctx, links_d, a, b, evals, evecs, psi, vol):
+    """Per-precision sign(K) rates and stencil bandwidth; solves to 1e-10."""
+    import torch
+    from paper_1510_06897_gb300.binding import (Ctx, ov_get_stats, ov_reset_stats, ov_set_profiling,
+                                                ov_sign_apply, ov_solve)
+    peaks, _ = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    res = {"precisions": {}}
+    out = torch.empty_like(psi)
+    for prec in ("fp64", "fp32", "fp16", "bf16"):
+        reps = 2 if prec == "fp64" else 8
+        with Ctx(DIMS, links_d, prec) as c:
+            c.sign_config(ORDER, a, b, evals, evecs)
+            ov_sign_apply(c.handle, psi, out, 1)
+            torch.cuda.synchronize()
+            ov_reset_stats(c.handle)
+            ov_set_profiling(c.handle, True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                ov_sign_apply(c.handle, psi, out, 1)
+            e1.record()
+            torch.cuda.synchronize()
+            ov_set_profiling(c.handle, False)
+            st = ov_get_stats(c.handle)
+        ms = e0.elapsed_time(e1) / reps
+        avg = st["dslash_ms"] / max(1, st["dslash_timed"])
+        gbs = stencil_bytes_per_apply(prec, ORDER, N_EV, vol) / (2 * ORDER + 1) / (avg * 1e-3) / 1e9
+        res["precisions"][prec] = {"applies_per_s": 1e3 / ms, "ms_per_apply": ms, "stencil_avg_us": avg * 1e3,
+                                   "stencil_GBps": gbs, "stencil_frac_of_hbm": gbs / hbm}
+    # time to solution, D^dagger D x = D^dagger b to 1e-10 (true residual, FP64 operator)
+    solves = {}
+    precs = [args.prec] + (["fp64"] if args.fp64_solve else [])
+    for prec in precs:
+        with Ctx(DIMS, links_d, prec) as c:
+            c.sign_config(ORDER, a, b, evals, evecs)
+            x = torch.empty_like(psi)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it, r = ov_solve(c.handle, MU, 1e-10, 20000, psi, x, 1, allow_not_converged=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            st = ov_get_stats(c.handle)
+        solves[prec] = {"seconds": dt, "iterations": it, "outer": st["outer_iterations"], "true_rel_resid": r,
+                        "mu": MU}
+    res["solve_1e-10"] = solves
+    return res
+
+
+if __name__ == "__main__":
+    main()

@@ -80,6 +80,8 @@ typedef struct {
   long long sign_applies;      /* sign(K) applications (per RHS) */
   long long inner_iterations;  /* CG iterations in the context's precision (last ov_solve) */
   long long outer_iterations;  /* FP64 defect-correction steps (last ov_solve) */
+  long long dslash_timed;      /* stencil launches timed while profiling was on */
+  double dslash_ms;            /* their summed device time (CUDA events on the context stream) */
 } ov_stats;
 
 /* Creates a context for one lattice and gauge field (Eq. 2 links).  Copies and
@@ -158,6 +160,12 @@ ov_status ov_eigs(ov_ctx* ctx, int n_ev, double tol, int max_iter, double* evals
  * backward with recomputation.  Errors: OV_ERR_INVALID. */
 ov_status ov_sign_poly_grad(ov_ctx* ctx, int order, double lo, double hi, const void* chi, void* grad_links,
                             ov_dtype dtype);
+
+/* Profiling of the stencil kernel: when on != 0, every stencil launch is
+ * bracketed by CUDA events on the context stream and its device time is added
+ * to ov_stats.dslash_ms (read back whenever a call synchronises).  Off by
+ * default; costs two event records per launch. */
+ov_status ov_set_profiling(ov_ctx* ctx, int on);
 
 ov_status ov_get_stats(const ov_ctx* ctx, ov_stats* out);
 ov_status ov_reset_stats(ov_ctx* ctx);

@@ -38,7 +38,9 @@ class ov_stats(ctypes.Structure):
                 ("dslash_launches", ctypes.c_longlong),
                 ("sign_applies", ctypes.c_longlong),
                 ("inner_iterations", ctypes.c_longlong),
-                ("outer_iterations", ctypes.c_longlong)]
+                ("outer_iterations", ctypes.c_longlong),
+                ("dslash_timed", ctypes.c_longlong),
+                ("dslash_ms", ctypes.c_double)]
 
 
 _LIB = None
@@ -61,6 +63,7 @@ _SIGNATURES = {
     "ov_sign_poly_grad": [_vp, _i, _d, _d, _vp, _vp, _i],
     "ov_get_stats": [_vp, ctypes.POINTER(ov_stats)],
     "ov_reset_stats": [_vp],
+    "ov_set_profiling": [_vp, _i],
 }
 
 
@@ -183,12 +186,14 @@ def ov_set_solver_params(ctx, inner_tol, max_outer):
     return _check(lib().ov_set_solver_params(ctx, float(inner_tol), int(max_outer)), ctx)
 
 
-def ov_eigs(ctx, n_ev, tol, max_iter, evecs):
+def ov_eigs(ctx, n_ev, tol, max_iter, evecs, allow_not_converged=False):
     """Fills evecs (complex128 (n_ev, ...)); returns (evals ndarray, lambda_max)."""
     evals = np.zeros(n_ev, dtype=np.float64)
     lmax = _d(0.0)
-    _check(lib().ov_eigs(ctx, int(n_ev), float(tol), int(max_iter), evals.ctypes.data_as(ctypes.POINTER(_d)),
-                         _ptr(evecs), ctypes.byref(lmax)), ctx)
+    st = lib().ov_eigs(ctx, int(n_ev), float(tol), int(max_iter), evals.ctypes.data_as(ctypes.POINTER(_d)),
+                       _ptr(evecs), ctypes.byref(lmax))
+    if not (allow_not_converged and st == OV_ERR_NOT_CONVERGED):
+        _check(st, ctx)
     return evals, lmax.value
 
 
@@ -201,6 +206,10 @@ def ov_get_stats(ctx):
     s = ov_stats()
     _check(lib().ov_get_stats(ctx, ctypes.byref(s)), ctx)
     return {name: getattr(s, name) for name, _ in ov_stats._fields_}
+
+
+def ov_set_profiling(ctx, on):
+    return _check(lib().ov_set_profiling(ctx, int(bool(on))), ctx)
 
 
 def ov_reset_stats(ctx):

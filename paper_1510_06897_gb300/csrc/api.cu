@@ -9,106 +9,22 @@
 #include <string>
 #include <vector>
 
-#include "../../include/overlap.h"
-#include "internal.h"
+#include "ctx.h"
 
 using namespace ov;
 
 namespace {
-
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-  cudaError_t ensure(size_t n) {
-    if (n <= bytes) return cudaSuccess;
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
-    cudaError_t e = cudaMalloc(&p, n);
-    if (e == cudaSuccess) bytes = n;
-    return e;
-  }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
-  }
-  template <class T> T* as() const { return static_cast<T*>(p); }
-  char* c() const { return static_cast<char*>(p); }
-};
-
-// One operator instance: links, eigenvectors and work vectors in one precision.
-struct Inst {
-  OpPrec p = OP_F64;   // link / recurrence storage
-  OpPrec pv = OP_F64;  // vector storage: deflation, assembly, solver vectors
-  bool active = false;
-  DevBuf links, evecs;
-  DevBuf xin, xout, d, tmp;          // pv
-  DevBuf perp, t, bA, bB;            // p
-  DevBuf cx, cr, cp, cq;             // pv: inner CG
-  size_t vbytes(int64_t V) const { return (size_t)spinor_bytes_per_site(pv) * V; }
-  size_t pbytes(int64_t V) const { return (size_t)spinor_bytes_per_site(p) * V; }
-  void release() {
-    for (DevBuf* b : {&links, &evecs, &xin, &xout, &d, &tmp, &perp, &t, &bA, &bB, &cx, &cr, &cp, &cq}) b->release();
-  }
-};
-
-enum Kind { K_SIGN, K_OVL, K_OVL_DAG };
-
 thread_local std::string g_create_error;
-
 }  // namespace
 
-struct ov_ctx {
-  LatticeH g{};
-  double m_w = 1.5;
-  cudaStream_t st = nullptr;
-  ov_prec prec = OV_FP64;
-  Inst hi;  // FP64 operator (always)
-  Inst lo;  // operator in the context precision when it is not FP64
-  // sign configuration
-  bool configured = false;
-  int order = 0;
-  double a = 0, b = 0;
-  std::vector<double> coef;
-  int n_ev = 0;
-  std::vector<double> evals, sgn;
-  DevBuf d_sgn, d_c, d_partial, d_scalars;
-  DevBuf stage_in, stage_out, stage_links;
-  DevBuf o_x, o_r, o_rhs, o_q;  // FP64 outer-solver vectors
-  double* h_scalars = nullptr;  // pinned
-  int h_scalars_n = 0;
-  // solver controls
-  double inner_tol = 1e-5;
-  int max_outer = 30;
-  ov_stats stats{};
-  std::string err;
-
-  Inst& op() { return prec == OV_FP64 ? hi : lo; }
-};
-
-namespace {
+namespace ov {
 
 ov_status fail(ov_ctx* c, ov_status s, const std::string& msg) {
   if (c) c->err = msg;
   return s;
 }
 
-#define OV_CK(call)                                                                             \
-  do {                                                                                          \
-    cudaError_t e_ = (call);                                                                    \
-    if (e_ != cudaSuccess)                                                                      \
-      return fail(c, e_ == cudaErrorMemoryAllocation ? OV_ERR_NOMEM : OV_ERR_CUDA,              \
-                  std::string(#call) + ": " + cudaGetErrorString(e_));                          \
-  } while (0)
-
-#define OV_TRY(expr)              \
-  do {                            \
-    ov_status s_ = (expr);        \
-    if (s_ != OV_OK) return s_;   \
-  } while (0)
-
-inline ov_status launched(ov_ctx* c, int n = 1) {
+ov_status launched(ov_ctx* c, int n) {
   c->stats.kernel_launches += n;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(c, OV_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
@@ -152,6 +68,41 @@ ov_status stage_out(ov_ctx* c, void* p, size_t bytes, void** out, bool* staged) 
 ov_status finish_out(ov_ctx* c, void* host, size_t bytes, bool staged) {
   if (staged) OV_CK(cudaMemcpyAsync(host, c->stage_out.p, bytes, cudaMemcpyDeviceToHost, c->st));
   OV_CK(cudaStreamSynchronize(c->st));
+  prof_collect(c);
+  return OV_OK;
+}
+
+void prof_collect(ov_ctx* c) {
+  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->evs[i], c->evs[i + 1]) == cudaSuccess) {
+      c->stats.dslash_ms += ms;
+      c->stats.dslash_timed++;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  c->ev_used = 0;
+}
+
+ov_status dslash(ov_ctx* c, OpPrec p, OpPrec out_prec, const void* links, const void* in, void* out,
+                 const EpiArgs& e, int nrhs) {
+  if (c->prof) {
+    while (c->evs.size() < c->ev_used + 2) {
+      cudaEvent_t ev;
+      OV_CK(cudaEventCreate(&ev));
+      c->evs.push_back(ev);
+    }
+    OV_CK(cudaEventRecord(c->evs[c->ev_used], c->st));
+  }
+  launch_dslash(p, out_prec, c->g, links, in, out, e, nrhs, c->st);
+  c->stats.dslash_launches++;
+  ov_status s = launched(c);
+  if (s != OV_OK) return s;
+  if (c->prof) {
+    OV_CK(cudaEventRecord(c->evs[c->ev_used + 1], c->st));
+    c->ev_used += 2;
+  }
   return OV_OK;
 }
 
@@ -178,6 +129,7 @@ ov_status read_reduced(ov_ctx* c, const double2* partial, int n, double2* out) {
   OV_TRY(launched(c));
   OV_CK(cudaMemcpyAsync(c->h_scalars, c->d_scalars.p, sizeof(double2) * n, cudaMemcpyDeviceToHost, c->st));
   OV_CK(cudaStreamSynchronize(c->st));
+  prof_collect(c);
   std::memcpy(out, c->h_scalars, sizeof(double2) * n);
   return OV_OK;
 }
@@ -219,9 +171,7 @@ std::vector<double> chebyshev_coefficients(int order, double a, double b) {
 
 // K applied to a recurrence vector: out (storage I.p) = s1 K in + sum w_j v_j.
 ov_status k_step(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, const EpiArgs& e) {
-  launch_dslash(I.p, I.p, c->g, I.links.p, in, out, e, nrhs, c->st);
-  c->stats.dslash_launches++;
-  return launched(c);
+  return dslash(c, I.p, I.p, I.links.p, in, out, e, nrhs);
 }
 
 // sign(K) / D[mu] / D[mu]^dagger on nrhs vectors in I.pv storage.
@@ -303,9 +253,7 @@ ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kin
     e.y = in;
     e.c0 = 0.5 * (1.0 + mu);
   }
-  launch_dslash(I.p, I.pv, c->g, I.links.p, h, out, e, nrhs, c->st);
-  c->stats.dslash_launches++;
-  OV_TRY(launched(c));
+  OV_TRY(dslash(c, I.p, I.pv, I.links.p, h, out, e, nrhs));
   c->stats.sign_applies += nrhs;
   return OV_OK;
 }
@@ -427,7 +375,7 @@ ov_status init_inst(ov_ctx* c, Inst& I, OpPrec p, const void* links_dev) {
   return launched(c);
 }
 
-}  // namespace
+}  // namespace ov
 
 // ===========================================================================
 // C ABI
@@ -495,6 +443,7 @@ ov_status ov_destroy(ov_ctx* c) {
   cudaStreamSynchronize(c->st);
   c->hi.release();
   c->lo.release();
+  for (cudaEvent_t ev : c->evs) cudaEventDestroy(ev);
   for (DevBuf* b : {&c->d_sgn, &c->d_c, &c->d_partial, &c->d_scalars, &c->stage_in, &c->stage_out, &c->stage_links,
                     &c->o_x, &c->o_r, &c->o_rhs, &c->o_q})
     b->release();
@@ -519,9 +468,7 @@ static ov_status apply_stencil(ov_ctx* c, const void* in, void* out, int nrhs, o
   EpiArgs e;
   e.wilson = wilson;
   e.m_w = c->m_w;
-  launch_dslash(I.p, I.pv, c->g, I.links.p, src, I.xout.p, e, nrhs, c->st);
-  c->stats.dslash_launches++;
-  OV_TRY(launched(c));
+  OV_TRY(dslash(c, I.p, I.pv, I.links.p, src, I.xout.p, e, nrhs));
   return unpack_output(c, I, I.xout.p, out, nrhs, dt);
 }
 
@@ -706,6 +653,16 @@ ov_status ov_solve(ov_ctx* c, double mu, double tol, int maxit, const void* b, v
 ov_status ov_get_stats(const ov_ctx* c, ov_stats* out) {
   if (!c || !out) return OV_ERR_INVALID;
   *out = c->stats;
+  return OV_OK;
+}
+
+ov_status ov_set_profiling(ov_ctx* c, int on) {
+  if (!c) return OV_ERR_INVALID;
+  if (!on && c->ev_used) {
+    OV_CK(cudaStreamSynchronize(c->st));
+    prof_collect(c);
+  }
+  c->prof = on ? 1 : 0;
   return OV_OK;
 }
 

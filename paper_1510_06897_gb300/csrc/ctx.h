@@ -1,0 +1,130 @@
+// Context of the C ABI and the host-side helpers shared by the drivers
+// (api.cu: operators and solver; eigs_host.cu: eigensolver; grad_host.cu:
+// adjoint).  Not part of the public interface.
+#pragma once
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/overlap.h"
+#include "internal.h"
+
+namespace ov {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t n) {
+    if (n <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e == cudaSuccess) bytes = n;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T> T* as() const { return static_cast<T*>(p); }
+  char* c() const { return static_cast<char*>(p); }
+};
+
+// One operator instance: links, eigenvectors and work vectors in one precision.
+struct Inst {
+  OpPrec p = OP_F64;   // link / recurrence storage
+  OpPrec pv = OP_F64;  // vector storage: deflation, assembly, solver vectors
+  bool active = false;
+  DevBuf links, evecs;
+  DevBuf xin, xout, d, tmp;          // pv
+  DevBuf perp, t, bA, bB;            // p
+  DevBuf cx, cr, cp, cq;             // pv: inner CG
+  size_t vbytes(int64_t V) const { return (size_t)spinor_bytes_per_site(pv) * V; }
+  size_t pbytes(int64_t V) const { return (size_t)spinor_bytes_per_site(p) * V; }
+  void release() {
+    for (DevBuf* b : {&links, &evecs, &xin, &xout, &d, &tmp, &perp, &t, &bA, &bB, &cx, &cr, &cp, &cq}) b->release();
+  }
+};
+
+enum Kind { K_SIGN, K_OVL, K_OVL_DAG };
+
+}  // namespace ov
+
+using namespace ov;
+
+struct ov_ctx {
+  LatticeH g{};
+  double m_w = 1.5;
+  cudaStream_t st = nullptr;
+  ov_prec prec = OV_FP64;
+  Inst hi;  // FP64 operator (always)
+  Inst lo;  // operator in the context precision when it is not FP64
+  // sign configuration
+  bool configured = false;
+  int order = 0;
+  double a = 0, b = 0;
+  std::vector<double> coef;
+  int n_ev = 0;
+  std::vector<double> evals, sgn;
+  DevBuf d_sgn, d_c, d_partial, d_scalars;
+  DevBuf stage_in, stage_out, stage_links;
+  DevBuf o_x, o_r, o_rhs, o_q;  // FP64 outer-solver vectors
+  double* h_scalars = nullptr;  // pinned
+  int h_scalars_n = 0;
+  // solver controls
+  double inner_tol = 1e-5;
+  int max_outer = 30;
+  ov_stats stats{};
+  std::string err;
+  // stencil profiling (ov_set_profiling)
+  int prof = 0;
+  std::vector<cudaEvent_t> evs;
+  size_t ev_used = 0;
+
+  Inst& op() { return prec == OV_FP64 ? hi : lo; }
+};
+
+
+namespace ov {
+
+ov_status fail(ov_ctx* c, ov_status s, const std::string& msg);
+ov_status launched(ov_ctx* c, int n = 1);
+ov_status stage_in(ov_ctx* c, DevBuf& buf, const void* p, size_t bytes, const void** out);
+ov_status stage_out(ov_ctx* c, void* p, size_t bytes, void** out, bool* staged);
+ov_status finish_out(ov_ctx* c, void* host, size_t bytes, bool staged);
+size_t iface_bytes(const LatticeH& g, int nrhs, ov_dtype dt);
+ov_status read_reduced(ov_ctx* c, const double2* partial, int n, double2* out);
+ov_status ensure_work(ov_ctx* c, Inst& I, int nrhs);
+ov_status norm2(ov_ctx* c, OpPrec p, const void* a, int64_t V, double* out);
+ov_status dots(ov_ctx* c, OpPrec p, const void* a, const void* b, int64_t V, double2* out);
+std::vector<double> chebyshev_coefficients(int order, double a, double b);
+ov_status pack_input(ov_ctx* c, Inst& I, const void* in, int nrhs, ov_dtype dt, void* dst);
+ov_status unpack_output(ov_ctx* c, Inst& I, const void* src, void* out, int nrhs, ov_dtype dt);
+ov_status check_dtype(ov_ctx* c, int nrhs, ov_dtype dt);
+// launch the stencil (counted, profiled when enabled)
+ov_status dslash(ov_ctx* c, OpPrec p, OpPrec out_prec, const void* links, const void* in, void* out,
+                 const EpiArgs& e, int nrhs);
+// fold completed profiling event pairs into the stats (call after a stream sync)
+void prof_collect(ov_ctx* c);
+// out (storage I.p) = stencil epilogue of K applied to `in` (see EpiArgs)
+ov_status k_step(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, const EpiArgs& e);
+ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kind kind, double mu, double scale);
+ov_status normal_apply(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, double mu, double scale);
+
+}  // namespace ov
+
+#define OV_CK(call)                                                                             \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return ov::fail(c, e_ == cudaErrorMemoryAllocation ? OV_ERR_NOMEM : OV_ERR_CUDA,          \
+                      std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+  } while (0)
+
+#define OV_TRY(expr)              \
+  do {                            \
+    ov_status s_ = (expr);        \
+    if (s_ != OV_OK) return s_;   \
+  } while (0)

@@ -1,0 +1,300 @@
+// ov_eigs: the lowest-|lambda| eigenpairs of K that the deflation of Eq. 3
+// needs (Sec. 2 precomputes them with a polynomial-preconditioned implicitly
+// restarted Lanczos).  Here: block subspace iteration on K^2 with a scaled
+// Chebyshev filter that damps [cut^2, b^2] (cut = largest Ritz value of the
+// block), Rayleigh-Ritz with K^2 (which orders the block and sets the filter
+// bounds), then Rayleigh-Ritz with K inside the lowest K^2 cluster so that
+// +lambda and -lambda split.
+// All inner products are FP64 sums; the m x m Hermitian eigenproblems are
+// solved on the host by cyclic Jacobi rotations.
+#include <algorithm>
+#include <complex>
+
+#include "ctx.h"
+
+using namespace ov;
+using cd = std::complex<double>;
+
+namespace {
+
+// Cyclic Jacobi for a Hermitian n x n matrix A (row-major, overwritten).
+// On return w holds the eigenvalues and V (row-major) the eigenvectors as columns.
+void herm_jacobi(int n, std::vector<cd>& A, std::vector<double>& w, std::vector<cd>& V) {
+  V.assign((size_t)n * n, cd(0.0));
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+  auto at = [&](int i, int j) -> cd& { return A[(size_t)i * n + j]; };
+  for (int i = 0; i < n; ++i) at(i, i) = cd(at(i, i).real(), 0.0);
+  double norm = 0.0;
+  for (const cd& x : A) norm += std::norm(x);
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) off += std::norm(at(i, j));
+    if (off <= 1e-30 * norm || off == 0.0) break;
+    for (int p = 0; p < n; ++p) {
+      for (int q = p + 1; q < n; ++q) {
+        const cd z = at(p, q);
+        const double r = std::abs(z);
+        if (r == 0.0) continue;
+        const cd ph = z / r;  // e^{i phi}
+        const double a = at(p, p).real(), b = at(q, q).real();
+        const double tau = (b - a) / (2.0 * r);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::abs(tau) + std::sqrt(1.0 + tau * tau));
+        const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = t * cs;
+        // G = diag(1, conj(ph)) * [[c, s], [-s, c]] on the (p, q) plane
+        const cd gpp = cs, gpq = sn, gqp = -sn * std::conj(ph), gqq = cs * std::conj(ph);
+        for (int k = 0; k < n; ++k) {  // A <- A G (columns p, q)
+          const cd akp = at(k, p), akq = at(k, q);
+          at(k, p) = akp * gpp + akq * gqp;
+          at(k, q) = akp * gpq + akq * gqq;
+        }
+        for (int k = 0; k < n; ++k) {  // A <- G^dagger A (rows p, q)
+          const cd apk = at(p, k), aqk = at(q, k);
+          at(p, k) = std::conj(gpp) * apk + std::conj(gqp) * aqk;
+          at(q, k) = std::conj(gpq) * apk + std::conj(gqq) * aqk;
+        }
+        at(p, q) = at(q, p) = 0.0;
+        at(p, p) = at(p, p).real();
+        at(q, q) = at(q, q).real();
+        for (int k = 0; k < n; ++k) {  // V <- V G
+          cd& vkp = V[(size_t)k * n + p];
+          cd& vkq = V[(size_t)k * n + q];
+          const cd a0 = vkp, b0 = vkq;
+          vkp = a0 * gpp + b0 * gqp;
+          vkq = a0 * gpq + b0 * gqq;
+        }
+      }
+    }
+  }
+  w.resize(n);
+  for (int i = 0; i < n; ++i) w[i] = at(i, i).real();
+}
+
+// Generalised Rayleigh-Ritz: eigenpairs of H in the metric G (both m x m
+// Hermitian): G = V g V^dag, S = V g^{-1/2}, S^dag H S = Q diag(w) Q^dag,
+// returns w ascending and C = S Q (row-major, columns = Ritz coefficients).
+void rayleigh_ritz(int m, const std::vector<cd>& G, const std::vector<cd>& H, std::vector<double>& w,
+                   std::vector<cd>& C) {
+  std::vector<cd> Gc = G;
+  std::vector<double> gw;
+  std::vector<cd> gv;
+  herm_jacobi(m, Gc, gw, gv);
+  double gmax = 0;
+  for (double x : gw) gmax = std::max(gmax, x);
+  std::vector<cd> S((size_t)m * m), T1((size_t)m * m, 0.0), Hp((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) S[(size_t)i * m + j] = gv[(size_t)i * m + j] / std::sqrt(std::max(gw[j], 1e-14 * gmax));
+  for (int i = 0; i < m; ++i)
+    for (int k = 0; k < m; ++k) {
+      const cd h = 0.5 * (H[(size_t)i * m + k] + std::conj(H[(size_t)k * m + i]));
+      for (int j = 0; j < m; ++j) T1[(size_t)i * m + j] += h * S[(size_t)k * m + j];
+    }
+  for (int i = 0; i < m; ++i)
+    for (int k = 0; k < m; ++k) {
+      const cd s = std::conj(S[(size_t)k * m + i]);
+      for (int j = 0; j < m; ++j) Hp[(size_t)i * m + j] += s * T1[(size_t)k * m + j];
+    }
+  std::vector<double> th;
+  std::vector<cd> q;
+  herm_jacobi(m, Hp, th, q);
+  std::vector<int> ord(m);
+  for (int i = 0; i < m; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int x, int y) { return th[x] != th[y] ? th[x] < th[y] : x < y; });
+  w.resize(m);
+  C.assign((size_t)m * m, 0.0);
+  for (int jj = 0; jj < m; ++jj) {
+    w[jj] = th[ord[jj]];
+    for (int i = 0; i < m; ++i) {
+      cd acc = 0.0;
+      for (int k = 0; k < m; ++k) acc += S[(size_t)i * m + k] * q[(size_t)k * m + ord[jj]];
+      C[(size_t)i * m + jj] = acc;
+    }
+  }
+}
+
+ov_status gram(ov_ctx* c, OpPrec p, const void* A, int ma, const void* B, int mb, DevBuf& partial,
+               std::vector<cd>& out) {
+  const int64_t V = c->g.V;
+  OV_CK(partial.ensure(sizeof(double2) * (size_t)ma * mb * kReduceBlocks));
+  OV_CK(launch_gram(p, A, ma, B, mb, V, partial.as<double2>(), kReduceBlocks, c->st));
+  OV_TRY(launched(c));
+  std::vector<double2> r((size_t)ma * mb);
+  OV_TRY(read_reduced(c, partial.as<double2>(), ma * mb, r.data()));
+  out.resize((size_t)ma * mb);
+  for (size_t i = 0; i < r.size(); ++i) out[i] = cd(r[i].x, r[i].y);
+  return OV_OK;
+}
+
+}  // namespace
+
+extern "C" ov_status ov_eigs(ov_ctx* c, int n_ev, double tol, int max_iter, double* evals, void* evecs,
+                             double* lambda_max_out) {
+  if (!c) return OV_ERR_INVALID;
+  if (!evals || !evecs) return fail(c, OV_ERR_INVALID, "null output");
+  const int mmax = gram_max_vectors();
+  if (n_ev < 1 || n_ev + 8 > mmax) return fail(c, OV_ERR_INVALID, "need 1 <= n_ev <= " + std::to_string(mmax - 8));
+  if (!(tol > 0.0) || max_iter < 1) return fail(c, OV_ERR_INVALID, "need tol > 0 and max_iter >= 1");
+  const int64_t V = c->g.V;
+  const int m = std::min(mmax, std::max(n_ev + 8, n_ev + n_ev / 2));
+  if ((int64_t)m > 12 * V) return fail(c, OV_ERR_INVALID, "block larger than the vector space");
+  Inst& I = (c->prec == OV_FP32) ? c->lo : c->hi;  // FP32 or FP64 storage (I.p == I.pv)
+  const OpPrec P = I.p;
+  const size_t vb = I.vbytes(V);
+  DevBuf bA, bB, bT, partial, dq;
+  OV_CK(bA.ensure(vb * m));
+  OV_CK(bB.ensure(vb * m));
+  OV_CK(bT.ensure(vb * m));
+  OV_TRY(ensure_work(c, I, 1));
+
+  launch_random_block(P, bA.p, m, V, 0x0ddc0ffeeull, c->st);
+  OV_TRY(launched(c));
+
+  // |lambda|_max: power iteration on K^2, then a safety margin; never below 6.5,
+  // which the free field attains.
+  double lam_est = 0.0;
+  {
+    double n0;
+    OV_TRY(norm2(c, P, bA.p, V, &n0));
+    launch_axpby(P, 1.0 / std::sqrt(n0), bA.p, 0.0, nullptr, bB.p, V, 1, c->st);
+    OV_TRY(launched(c));
+    for (int it = 0; it < 30; ++it) {
+      EpiArgs e;
+      e.m_w = c->m_w;
+      OV_TRY(k_step(c, I, bB.p, bT.p, 1, e));
+      OV_TRY(k_step(c, I, bT.p, I.tmp.p, 1, e));
+      double2 rq;
+      OV_TRY(dots(c, P, bB.p, I.tmp.p, V, &rq));
+      lam_est = std::sqrt(std::max(rq.x, 0.0));
+      double nn;
+      OV_TRY(norm2(c, P, I.tmp.p, V, &nn));
+      launch_axpby(P, 1.0 / std::sqrt(nn), I.tmp.p, 0.0, nullptr, bB.p, V, 1, c->st);
+      OV_TRY(launched(c));
+    }
+  }
+  const double bmax = std::max(6.5, 1.02 * lam_est);
+  const double b2 = bmax * bmax;
+
+  std::vector<double> theta(m, 0.0), res(m, 1.0);
+  double cut2 = b2 * 0.5, low2 = 0.0;
+  void* Y = bA.p;  // current block
+  void* Z = bB.p;  // scratch block
+  bool converged = false;
+  int iter = 0;
+  const int degree = 16;
+  for (; iter < max_iter; ++iter) {
+    if (iter > 0) {
+      // scaled Chebyshev filter on K^2 damping [cut2, b2], normalised at low2
+      const double e = 0.5 * (b2 - cut2), cc = 0.5 * (b2 + cut2);
+      double sigma = e / (low2 - cc);
+      const double sigma1 = sigma, gam = 2.0 / sigma1;
+      EpiArgs ek;
+      ek.m_w = c->m_w;
+      OV_TRY(k_step(c, I, Y, bT.p, m, ek));
+      EpiArgs e1;
+      e1.m_w = c->m_w;
+      e1.s1 = sigma / e;
+      e1.v[0] = Y;
+      e1.w[0] = -sigma * cc / e;
+      OV_TRY(k_step(c, I, bT.p, Z, m, e1));
+      void* y0 = Y;
+      void* y1 = Z;
+      for (int k = 2; k <= degree; ++k) {
+        const double sn = 1.0 / (gam - sigma);
+        OV_TRY(k_step(c, I, y1, bT.p, m, ek));
+        EpiArgs e2;
+        e2.m_w = c->m_w;
+        e2.s1 = 2.0 * sn / e;
+        e2.v[0] = y1;
+        e2.w[0] = -2.0 * sn * cc / e;
+        e2.v[1] = y0;
+        e2.w[1] = -sigma * sn;
+        OV_TRY(k_step(c, I, bT.p, y0, m, e2));  // y0 <- new (in place over y_{k-2})
+        std::swap(y0, y1);
+        sigma = sn;
+      }
+      Y = y1;
+      Z = y0;
+    }
+    // Rayleigh-Ritz with K^2 in span(Y): G = Y^dag Y, W = K Y, H2 = W^dag W.
+    // (Rayleigh-Ritz with the indefinite K itself would produce spurious
+    // near-zero Ritz values from mixtures of +lambda and -lambda modes.)
+    EpiArgs ek;
+    ek.m_w = c->m_w;
+    OV_TRY(k_step(c, I, Y, bT.p, m, ek));
+    std::vector<cd> G, H2;
+    OV_TRY(gram(c, P, Y, m, Y, m, partial, G));
+    OV_TRY(gram(c, P, bT.p, m, bT.p, m, partial, H2));
+    std::vector<double> th2;
+    std::vector<cd> C2;
+    rayleigh_ritz(m, G, H2, th2, C2);
+    std::vector<double2> C((size_t)m * m);
+    for (size_t i = 0; i < C.size(); ++i) C[i] = make_double2(C2[i].real(), C2[i].imag());
+    OV_CK(dq.ensure(sizeof(double2) * m * m));
+    OV_CK(cudaMemcpyAsync(dq.p, C.data(), sizeof(double2) * m * m, cudaMemcpyHostToDevice, c->st));
+    launch_rotate(P, Y, m, dq.as<double2>(), m, Z, V, c->st);  // Z = Y C
+    OV_TRY(launched(c));
+    launch_rotate(P, bT.p, m, dq.as<double2>(), m, Y, V, c->st);  // Y = (K Y) C
+    OV_TRY(launched(c));
+    std::swap(Y, Z);  // Y: K^2-Ritz vectors (ascending), Z: K times them
+    // Split +lambda / -lambda: Rayleigh-Ritz with K inside the lowest K^2
+    // cluster that contains the wanted n_ev vectors.
+    int p = n_ev;
+    while (p < m && th2[p] - th2[p - 1] < 1e-3 * th2[p - 1]) ++p;
+    std::vector<cd> H1;
+    OV_TRY(gram(c, P, Y, p, Z, p, partial, H1));
+    for (int i = 0; i < p; ++i)
+      for (int j = i; j < p; ++j) {
+        const cd h = 0.5 * (H1[(size_t)i * p + j] + std::conj(H1[(size_t)j * p + i]));
+        H1[(size_t)i * p + j] = h;
+        H1[(size_t)j * p + i] = std::conj(h);
+      }
+    std::vector<double> th;
+    std::vector<cd> q;
+    herm_jacobi(p, H1, th, q);
+    std::vector<int> ord(p);
+    for (int i = 0; i < p; ++i) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](int x, int y) {
+      const double ax = std::abs(th[x]), ay = std::abs(th[y]);
+      return ax != ay ? ax < ay : (th[x] != th[y] ? th[x] < th[y] : x < y);
+    });
+    std::vector<double2> Q1((size_t)p * p);
+    for (int i = 0; i < p; ++i)
+      for (int jj = 0; jj < p; ++jj) {
+        const cd v = q[(size_t)i * p + ord[jj]];
+        Q1[(size_t)i * p + jj] = make_double2(v.real(), v.imag());
+      }
+    for (int jj = 0; jj < p; ++jj) theta[jj] = th[ord[jj]];
+    for (int jj = p; jj < m; ++jj) theta[jj] = std::sqrt(std::max(th2[jj], 0.0));
+    OV_CK(cudaMemcpyAsync(dq.p, Q1.data(), sizeof(double2) * p * p, cudaMemcpyHostToDevice, c->st));
+    for (void* blk : {Y, Z}) {
+      launch_rotate(P, blk, p, dq.as<double2>(), p, bT.p, V, c->st);
+      OV_TRY(launched(c));
+      OV_CK(cudaMemcpyAsync(blk, bT.p, vb * p, cudaMemcpyDeviceToDevice, c->st));
+    }
+    // residuals ||K y_j - theta_j y_j||
+    double worst = 0.0;
+    for (int j = 0; j < n_ev; ++j) {
+      launch_axpby(P, 1.0, static_cast<char*>(Z) + j * vb, -theta[j], static_cast<char*>(Y) + j * vb, I.tmp.p, V, 1,
+                   c->st);
+      OV_TRY(launched(c));
+      double r2;
+      OV_TRY(norm2(c, P, I.tmp.p, V, &r2));
+      res[j] = std::sqrt(r2);
+      worst = std::max(worst, res[j]);
+    }
+    low2 = th2[0];
+    cut2 = std::max(th2[m - 1], low2 * 1.0001 + 1e-12);
+    if (cut2 >= b2 * 0.999) cut2 = 0.5 * (low2 + b2);
+    if (worst <= tol * bmax) {
+      converged = true;
+      ++iter;
+      break;
+    }
+  }
+  for (int j = 0; j < n_ev; ++j) evals[j] = theta[j];
+  if (lambda_max_out) *lambda_max_out = bmax;
+  OV_TRY(unpack_output(c, I, Y, evecs, n_ev, OV_C128));
+  for (DevBuf* b : {&bA, &bB, &bT, &partial, &dq}) b->release();
+  if (!converged) return fail(c, OV_ERR_NOT_CONVERGED, "eigensolver: max_iter reached before tol");
+  return OV_OK;
+}

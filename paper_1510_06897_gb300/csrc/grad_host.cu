@@ -1,0 +1,190 @@
+// ov_sign_poly_grad: gradient of S = chi^dagger P(K) chi with respect to the
+// links, P(K) = K f_N(K^2) the undeflated polynomial of Eq. 3.
+//
+// Forward: the Clenshaw recurrence b_k = c_k chi + 2 Z b_{k+1} - b_{k+2}
+// (k = N..0), g = (b_0 - b_2)/2, S = (K chi)^dagger g, keeping (b_k) for
+// k = 1, 2 mod 16 as checkpoints.  Reverse: with gbar = K chi the adjoint
+// vectors obey bbar_0 = gbar/2, bbar_1 = 2 Z bbar_0,
+// bbar_2 = 2 Z bbar_1 - bbar_0 - gbar/2, bbar_j = 2 Z bbar_{j-1} - bbar_{j-2},
+// and
+//   dS = chi^dagger dK g + sum_{k=0}^{N-1} 2 bbar_k^dagger dZ b_{k+1},
+//   dZ = alpha (dK K + K dK),
+// so each step k contributes the dK pairs (bbar_k, K b_{k+1}) and
+// (K bbar_k, b_{k+1}) with weight 2 alpha.  The adjoint runs upward in k
+// while the recurrence produced b_k downward, so b_{k+1} and K b_{k+1} are
+// recomputed 16 at a time from the checkpoints, and each segment's 32 pairs
+// are folded into the link accumulator by one force launch.
+#include "ctx.h"
+
+using namespace ov;
+
+namespace {
+constexpr int kSeg = 16;
+}
+
+extern "C" ov_status ov_sign_poly_grad(ov_ctx* c, int order, double lo, double hi, const void* chi,
+                                       void* grad_links, ov_dtype dt) {
+  if (!c) return OV_ERR_INVALID;
+  if (!chi || !grad_links) return fail(c, OV_ERR_INVALID, "null argument");
+  if (order < 1) return fail(c, OV_ERR_INVALID, "Chebyshev order must be >= 1");
+  if (!(lo > 0.0) || !(hi > lo) || !std::isfinite(hi)) return fail(c, OV_ERR_INVALID, "need 0 < lo < hi");
+  OV_TRY(check_dtype(c, 1, dt));
+  if (c->prec != OV_FP64 && c->prec != OV_FP32)
+    return fail(c, OV_ERR_INVALID, "ov_sign_poly_grad needs an OV_FP64 or OV_FP32 context");
+  Inst& I = (c->prec == OV_FP64) ? c->hi : c->lo;
+  const OpPrec P = I.p;  // == I.pv
+  const int64_t V = c->g.V;
+  const size_t vb = I.vbytes(V);
+  const int N = order;
+  const std::vector<double> cf = chebyshev_coefficients(N, lo, hi);
+  const double a2 = lo * lo, b2 = hi * hi;
+  const double alpha = 2.0 / (b2 - a2), beta = -(b2 + a2) / (b2 - a2);
+
+  // checkpoint slots: k = 16 j + 1 -> 2 j, k = 16 j + 2 -> 2 j + 1
+  const int nck = 2 * (N / kSeg + 2);
+  DevBuf xchi, ck, segb, segt, bbar, tbar, gvec, gbar, zero, t, G;
+  OV_CK(xchi.ensure(vb));
+  OV_CK(ck.ensure(vb * nck));
+  OV_CK(segb.ensure(vb * (kSeg + 2)));
+  OV_CK(segt.ensure(vb * (kSeg + 1)));
+  OV_CK(bbar.ensure(vb * (kSeg + 2)));
+  OV_CK(tbar.ensure(vb * kSeg));
+  OV_CK(gvec.ensure(vb));
+  OV_CK(gbar.ensure(vb));
+  OV_CK(zero.ensure(vb));
+  OV_CK(t.ensure(vb));
+  const size_t gbytes = (size_t)4 * 9 * V * (P == OP_F64 ? 16 : 8);
+  OV_CK(G.ensure(gbytes));
+  OV_CK(cudaMemsetAsync(zero.p, 0, vb, c->st));
+  OV_CK(cudaMemsetAsync(G.p, 0, gbytes, c->st));
+  OV_TRY(pack_input(c, I, chi, 1, dt, xchi.p));
+  auto slot = [&](DevBuf& b, int i) { return static_cast<void*>(b.c() + (size_t)i * vb); };
+  auto ck_slot = [&](int k) -> void* {
+    if (k > N) return zero.p;
+    if (k % kSeg == 1) return slot(ck, 2 * (k / kSeg));
+    if (k % kSeg == 2) return slot(ck, 2 * (k / kSeg) + 1);
+    return nullptr;
+  };
+  EpiArgs ek;
+  ek.m_w = c->m_w;
+
+  // One Clenshaw step: out = c_k chi + 2 alpha K (K bk1) + 2 beta bk1 - bk2 (tk1 = K bk1 kept).
+  auto clenshaw = [&](int k, const void* bk1, const void* bk2, void* tk1, void* out) -> ov_status {
+    OV_TRY(k_step(c, I, bk1, tk1, 1, ek));
+    EpiArgs e;
+    e.m_w = c->m_w;
+    e.s1 = 2.0 * alpha;
+    e.v[0] = bk1;
+    e.w[0] = 2.0 * beta;
+    e.v[1] = bk2;
+    e.w[1] = -1.0;
+    e.v[2] = xchi.p;
+    e.w[2] = cf[k];
+    return k_step(c, I, tk1, out, 1, e);
+  };
+
+  // ---- forward sweep: b_k for k = N .. 0, rotating through three vectors
+  void* rot[3] = {slot(segb, 0), slot(segb, 1), slot(segb, 2)};
+  const void* bk1 = zero.p;  // b_{k+1}
+  const void* bk2 = zero.p;  // b_{k+2}
+  void* b0 = nullptr;
+  void* b2v = nullptr;
+  for (int k = N; k >= 0; --k) {
+    void* out = rot[k % 3];
+    OV_TRY(clenshaw(k, bk1, bk2, t.p, out));
+    if (void* cs = (k >= 1) ? ck_slot(k) : nullptr) {
+      OV_CK(cudaMemcpyAsync(cs, out, vb, cudaMemcpyDeviceToDevice, c->st));
+    }
+    if (k == 2) b2v = out;
+    if (k == 0) b0 = out;
+    bk2 = bk1;
+    bk1 = out;
+  }
+  // g = (b_0 - b_2)/2 ; gbar = K chi
+  launch_axpby(P, 0.5, b0, -0.5, b2v, gvec.p, V, 1, c->st);
+  OV_TRY(launched(c));
+  OV_TRY(k_step(c, I, xchi.p, gbar.p, 1, ek));
+
+  // ---- reverse sweep, one segment of 16 adjoint steps at a time
+  // bbar slots: slot(bbar, k - k0 + 1) holds bbar_k for k in [k0-1, k0+16]
+  OV_CK(cudaMemsetAsync(slot(bbar, 0), 0, vb, c->st));  // bbar_{-1} = 0
+  launch_axpby(P, 0.5, gbar.p, 0.0, nullptr, slot(bbar, 1), V, 1, c->st);  // bbar_0
+  OV_TRY(launched(c));
+  bool first_pair = true;
+  for (int k0 = 0; k0 < N; k0 += kSeg) {
+    const int k1 = std::min(k0 + kSeg, N) - 1;  // last adjoint step of the segment
+    if (k0 > 0) {
+      OV_CK(cudaMemcpyAsync(slot(bbar, 0), slot(bbar, kSeg), vb, cudaMemcpyDeviceToDevice, c->st));
+      OV_CK(cudaMemcpyAsync(slot(bbar, 1), slot(bbar, kSeg + 1), vb, cudaMemcpyDeviceToDevice, c->st));
+    }
+    // recompute b_j and t_j = K b_j for j = k0+1 .. k1+1 (segb/segt slot j - k0 - 1)
+    {
+      const int top = k1 + 1;
+      // from b_{k0+17}, b_{k0+18} (checkpoints; zero above N) down to b_{k0+1}
+      const void* p1 = ck_slot(k0 + kSeg + 1);
+      const void* p2 = ck_slot(k0 + kSeg + 2);
+      for (int j = k0 + kSeg; j >= k0 + 1; --j) {
+        if (j > N) {  // b_j = 0 above the top coefficient
+          p2 = p1;
+          p1 = zero.p;
+          continue;
+        }
+        void* dst = slot(segb, j - k0 - 1);
+        void* tj1 = (j + 1 <= top) ? slot(segt, j - k0) : t.p;
+        OV_TRY(clenshaw(j, p1, p2, tj1, dst));
+        p2 = p1;
+        p1 = dst;
+      }
+      // t_{k0+1} = K b_{k0+1}
+      OV_TRY(k_step(c, I, slot(segb, 0), slot(segt, 0), 1, ek));
+    }
+    // adjoint steps k = k0 .. k1
+    ForcePairs pairs;
+    if (first_pair) {
+      pairs.u[pairs.n] = xchi.p;
+      pairs.v[pairs.n] = gvec.p;
+      pairs.w[pairs.n] = 1.0;
+      pairs.n++;
+      first_pair = false;
+    }
+    for (int k = k0; k <= k1; ++k) {
+      void* bb_k = slot(bbar, k - k0 + 1);
+      void* bb_km1 = slot(bbar, k - k0);
+      void* tb_k = slot(tbar, k - k0);
+      OV_TRY(k_step(c, I, bb_k, tb_k, 1, ek));  // tbar_k = K bbar_k
+      pairs.u[pairs.n] = bb_k;
+      pairs.v[pairs.n] = slot(segt, k - k0);  // t_{k+1}
+      pairs.w[pairs.n] = 2.0 * alpha;
+      pairs.n++;
+      pairs.u[pairs.n] = tb_k;
+      pairs.v[pairs.n] = slot(segb, k - k0);  // b_{k+1}
+      pairs.w[pairs.n] = 2.0 * alpha;
+      pairs.n++;
+      if (k + 1 <= N - 1) {  // bbar_{k+1} = 2 alpha K tbar_k + 2 beta bbar_k - bbar_{k-1} [- gbar/2 at k+1 = 2]
+        EpiArgs e;
+        e.m_w = c->m_w;
+        e.s1 = 2.0 * alpha;
+        e.v[0] = bb_k;
+        e.w[0] = 2.0 * beta;
+        e.v[1] = bb_km1;
+        e.w[1] = -1.0;
+        if (k + 1 == 2) {
+          e.v[2] = gbar.p;
+          e.w[2] = -0.5;
+        }
+        OV_TRY(k_step(c, I, tb_k, slot(bbar, k - k0 + 2), 1, e));
+      }
+    }
+    launch_force_pairs(P, c->g, I.links.p, pairs, G.p, c->st);
+    OV_TRY(launched(c));
+  }
+  void* dout;
+  bool staged;
+  const size_t obytes = (size_t)4 * V * 9 * 16;
+  OV_TRY(stage_out(c, grad_links, obytes, &dout, &staged));
+  launch_force_finish(P, G.p, V, dout, c->st);
+  OV_TRY(launched(c));
+  OV_TRY(finish_out(c, grad_links, obytes, staged));
+  for (DevBuf* b : {&xchi, &ck, &segb, &segt, &bbar, &tbar, &gvec, &gbar, &zero, &t, &G}) b->release();
+  return OV_OK;
+}

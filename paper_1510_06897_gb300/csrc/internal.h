@@ -101,4 +101,31 @@ void launch_axpby(OpPrec p, double a, const void* x, double b, const void* y, vo
 void launch_convert(OpPrec pi, OpPrec po, const void* in, void* out, int64_t V, int nrhs, double scale,
                     int accumulate, cudaStream_t st);
 
+// ---- eigensolver block kernels (eigs.cu) ------------------------------------
+// Block storage: m vectors of V sites back to back, storage OP_F64 or OP_F32.
+void launch_random_block(OpPrec p, void* out, int m, int64_t V, uint64_t seed, cudaStream_t st);
+// partial[(i*mb + j)*nblk + blk] = block blk's share of <A_i, B_j>; ma, mb <= gram_max_vectors().
+cudaError_t launch_gram(OpPrec p, const void* A, int ma, const void* B, int mb, int64_t V, double2* partial,
+                        int nblk, cudaStream_t st);
+int gram_max_vectors();
+// out_j = sum_i Y_i Q[i*m_out + j]   (Q complex FP64 on the device; out must not alias Y)
+void launch_rotate(OpPrec p, const void* Y, int m_in, const double2* Q, int m_out, void* out, int64_t V,
+                   cudaStream_t st);
+
+// ---- link derivative (force.cu) ------------------------------------------------
+// G_mu(x) += sum_p w_p * (colour outer products of pair p), see force.cu.
+constexpr int kMaxForcePairs = 34;
+struct ForcePairs {
+  const void* u[kMaxForcePairs];
+  const void* v[kMaxForcePairs];
+  double w[kMaxForcePairs];
+  int n = 0;
+};
+// G: complex [4][9][V] in the arithmetic type of p (OP_F64 or OP_F32); pair
+// vectors in the same storage.
+void launch_force_pairs(OpPrec p, const LatticeH& g, const void* links, const ForcePairs& pairs, void* G,
+                        cudaStream_t st);
+// out: complex128 AoS [4][V][3][3] = P_TA(G^dagger)
+void launch_force_finish(OpPrec p, const void* G, int64_t V, void* out, cudaStream_t st);
+
 }  // namespace ov

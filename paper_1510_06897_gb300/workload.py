@@ -1,0 +1,64 @@
+"""Seeded overlap workloads for profiling runs (ncu launch lists and captures).
+
+  python -m paper_1510_06897_gb300.workload --lattice 24,24,24,48 --prec fp16 \
+      --order 256 --n-ev 40 --applies 3
+
+builds the seeded links (exp(i 0.3 H)), takes n_ev orthonormal vectors from a
+single Rayleigh-Ritz pass of ov_eigs (the same amount of deflation work as
+converged eigenvectors; the eigensolver itself is left out of the profile),
+configures sign(K) on [lo, hi] and runs `applies` sign(K) applications (or
+D^dagger D solves with --solve), all through the C ABI.
+"""
+import argparse
+import sys
+import time
+
+
+def main(argv=None):
+    import torch
+
+    from . import inputs
+    from .binding import Ctx, ov_eigs, ov_get_stats, ov_sign_apply, ov_solve
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--lattice", default="24,24,24,48")
+    ap.add_argument("--prec", default="fp16", choices=["fp64", "fp32", "fp16", "bf16"])
+    ap.add_argument("--order", type=int, default=256)
+    ap.add_argument("--n-ev", type=int, default=40)
+    ap.add_argument("--lo", type=float, default=0.5)
+    ap.add_argument("--hi", type=float, default=6.5)
+    ap.add_argument("--applies", type=int, default=3)
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--solve", action="store_true")
+    ap.add_argument("--mu", type=float, default=0.02)
+    args = ap.parse_args(argv)
+
+    dims = tuple(int(x) for x in args.lattice.split(","))
+    fshape = (dims[3], dims[2], dims[1], dims[0], 4, 3)
+    links = torch.from_numpy(inputs.gauge_links(dims, seed=1003)).cuda()
+    psi = torch.from_numpy(inputs.gaussian_source(dims, seed=2003, nrhs=args.nrhs)).cuda()
+    evals, evecs = None, None
+    if args.n_ev > 0:
+        evecs = torch.zeros((args.n_ev,) + fshape, dtype=torch.complex128, device="cuda")
+        with Ctx(dims, links, "fp32" if args.prec != "fp64" else "fp64") as c:
+            evals, _ = ov_eigs(c.handle, args.n_ev, 1e-12, 1, evecs, allow_not_converged=True)
+    with Ctx(dims, links, args.prec) as c:
+        c.sign_config(args.order, args.lo, args.hi, evals, evecs)
+        out = torch.empty_like(psi)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.applies):
+            if args.solve:
+                it, res = ov_solve(c.handle, args.mu, 1e-10, 20000, psi, out, args.nrhs, allow_not_converged=True)
+                print(f"solve: {it} iterations, true residual {res:.3e}")
+            else:
+                ov_sign_apply(c.handle, psi, out, args.nrhs)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        print(f"{args.applies} x {'solve' if args.solve else 'sign apply'} ({args.prec}, {args.lattice}, "
+              f"order {args.order}, n_ev {args.n_ev}, nrhs {args.nrhs}): {dt / args.applies * 1e3:.2f} ms each; "
+              f"stats {ov_get_stats(c.handle)}", flush=True)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,74 @@
+"""Host-only checks of the C ABI: the library builds, loads without a GPU and
+exports every function include/overlap.h declares; argument validation that
+happens before any device work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1510_06897_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "overlap.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ov_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for fn in ("ov_create", "ov_destroy", "ov_wilson", "ov_sign", "ov_overlap", "ov_solve", "ov_eigs",
+               "ov_sign_poly_grad", "ov_last_error"):
+        assert fn in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    raw = ctypes.CDLL(build.LIB_PATH)
+    missing = [n for n in _declared() if not hasattr(raw, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("dims", [(1, 4, 4, 4), (4, 4, 0, 4), (4, 4, 4, -2)])
+def test_create_rejects_bad_dims_before_device_work(lib, dims):
+    links = np.zeros((4, 1, 1, 1, 1, 3, 3), dtype=np.complex128)
+    with pytest.raises(binding.OverlapError) as e:
+        binding.ov_create(dims, links)
+    assert e.value.status == binding.OV_ERR_INVALID
+    assert "extent" in binding.ov_last_error(None)
+
+
+def test_create_rejects_bad_precision_and_null(lib):
+    links = np.zeros((4, 2, 2, 2, 2, 3, 3), dtype=np.complex128)
+    with pytest.raises(binding.OverlapError):
+        binding.ov_create((2, 2, 2, 2), links, prec=7)
+    handle = ctypes.c_void_p()
+    dims = (ctypes.c_int * 4)(2, 2, 2, 2)
+    assert lib.ov_create(ctypes.byref(handle), dims, None, 0, 1.5, 0, None) == binding.OV_ERR_INVALID
+    assert lib.ov_create(None, dims, links.ctypes.data, 0, 1.5, 0, None) == binding.OV_ERR_INVALID
+
+
+def test_null_context_calls(lib):
+    assert lib.ov_destroy(None) == binding.OV_OK
+    assert lib.ov_wilson(None, None, None, 1, 0) == binding.OV_ERR_INVALID
+    assert lib.ov_sign_apply(None, None, None, 1, 0) == binding.OV_ERR_INVALID
+    assert lib.ov_solve(None, 0.1, 1e-10, 10, None, None, 1, 0, None, None) == binding.OV_ERR_INVALID
+    assert lib.ov_get_stats(None, None) == binding.OV_ERR_INVALID
+
+
+def test_binding_dtype_codes():
+    assert binding._dtype_code(np.zeros(2, np.complex128)) == binding.OV_C128
+    assert binding._dtype_code(np.zeros(2, np.complex64)) == binding.OV_C64
+    with pytest.raises(TypeError):
+        binding._dtype_code(np.zeros(2, np.float64))
+    with pytest.raises(ValueError):
+        binding._ptr(np.zeros((4, 4), np.complex128)[:, ::2])
