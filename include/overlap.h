@@ -82,6 +82,10 @@ typedef struct {
   long long outer_iterations;  /* FP64 defect-correction steps (last ov_solve) */
   long long dslash_timed;      /* stencil launches timed while profiling was on */
   double dslash_ms;            /* their summed device time (CUDA events on the context stream) */
+  int stencil_tpb;             /* autotuned stencil launch of the context-precision operator: */
+  int stencil_minb;            /*   threads per block, register cap (2/3/4 = 128/85/64 regs), */
+  int stencil_lrec;            /*   stored reals per link (12: row 2 rebuilt, 18: all) */
+  int reserved;
 } ov_stats;
 
 /* Creates a context for one lattice and gauge field (Eq. 2 links).  Copies and
@@ -90,7 +94,10 @@ typedef struct {
  * antiperiodic_t != 0: fermion boundary condition antiperiodic in t (periodic
  * otherwise).  cuda_stream: a cudaStream_t (NULL = legacy default stream).
  * Errors: OV_ERR_INVALID (null ctx/dims/links, any L < 2, bad prec),
- * OV_ERR_NOMEM, OV_ERR_CUDA. */
+ * OV_ERR_NOMEM, OV_ERR_CUDA.
+ * The stencil's launch shape and (16-bit) link layout are autotuned here by
+ * timing a few launches of each variant on this lattice; the environment
+ * variable OV_STENCIL="tpb,minb,lrec" pins one variant instead (see ov_stats). */
 ov_status ov_create(ov_ctx** ctx, const int dims[4], const void* links, ov_prec prec, double m_w,
                     int antiperiodic_t, void* cuda_stream);
 

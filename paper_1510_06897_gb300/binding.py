@@ -40,7 +40,11 @@ class ov_stats(ctypes.Structure):
                 ("inner_iterations", ctypes.c_longlong),
                 ("outer_iterations", ctypes.c_longlong),
                 ("dslash_timed", ctypes.c_longlong),
-                ("dslash_ms", ctypes.c_double)]
+                ("dslash_ms", ctypes.c_double),
+                ("stencil_tpb", ctypes.c_int),
+                ("stencil_minb", ctypes.c_int),
+                ("stencil_lrec", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
 
 _LIB = None

@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <cstdlib>
+
 #include "ctx.h"
 
 using namespace ov;
@@ -85,8 +87,7 @@ void prof_collect(ov_ctx* c) {
   c->ev_used = 0;
 }
 
-ov_status dslash(ov_ctx* c, OpPrec p, OpPrec out_prec, const void* links, const void* in, void* out,
-                 const EpiArgs& e, int nrhs) {
+ov_status dslash(ov_ctx* c, Inst& I, OpPrec out_prec, const void* in, void* out, const EpiArgs& e, int nrhs) {
   if (c->prof) {
     while (c->evs.size() < c->ev_used + 2) {
       cudaEvent_t ev;
@@ -95,7 +96,7 @@ ov_status dslash(ov_ctx* c, OpPrec p, OpPrec out_prec, const void* links, const 
     }
     OV_CK(cudaEventRecord(c->evs[c->ev_used], c->st));
   }
-  launch_dslash(p, out_prec, c->g, links, in, out, e, nrhs, c->st);
+  launch_dslash(I.p, out_prec, I.cfg, c->g, I.links.p, in, out, e, nrhs, c->st);
   c->stats.dslash_launches++;
   ov_status s = launched(c);
   if (s != OV_OK) return s;
@@ -171,7 +172,7 @@ std::vector<double> chebyshev_coefficients(int order, double a, double b) {
 
 // K applied to a recurrence vector: out (storage I.p) = s1 K in + sum w_j v_j.
 ov_status k_step(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, const EpiArgs& e) {
-  return dslash(c, I.p, I.p, I.links.p, in, out, e, nrhs);
+  return dslash(c, I, I.p, in, out, e, nrhs);
 }
 
 // sign(K) / D[mu] / D[mu]^dagger on nrhs vectors in I.pv storage.
@@ -253,7 +254,7 @@ ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kin
     e.y = in;
     e.c0 = 0.5 * (1.0 + mu);
   }
-  OV_TRY(dslash(c, I.p, I.pv, I.links.p, h, out, e, nrhs));
+  OV_TRY(dslash(c, I, I.pv, h, out, e, nrhs));
   c->stats.sign_applies += nrhs;
   return OV_OK;
 }
@@ -366,13 +367,101 @@ ov_status unpack_output(ov_ctx* c, Inst& I, const void* src, void* out, int nrhs
   return finish_out(c, out, bytes, staged);
 }
 
+// Times the stencil variants (threads per block, register cap, and for 16-bit
+// links the 12- or 18-real layout) on this lattice with a plain K step and a
+// recurrence step, and keeps the fastest.
+// The environment variable OV_STENCIL="tpb,minb,lrec" (e.g. "192,3,12")
+// skips the timing and pins one variant (used for reproducible profiles).
+ov_status autotune(ov_ctx* c, Inst& I, const void* links_dev) {
+  const int64_t V = c->g.V;
+  I.cfg = DslashCfg{};
+  const bool is16 = (I.p == OP_F16 || I.p == OP_B16);
+  if (const char* env = std::getenv("OV_STENCIL")) {
+    int tpb = 0, minb = 0, lrec = 0;
+    if (std::sscanf(env, "%d,%d,%d", &tpb, &minb, &lrec) == 3 && tpb >= 32 && tpb <= 256 && tpb % 32 == 0 &&
+        minb >= 2 && minb <= 4 && (lrec == 12 || lrec == 18)) {
+      I.cfg = DslashCfg{tpb, minb, is16 ? lrec : 12};
+      if (is16 && lrec == 18) {
+        DevBuf full;
+        OV_CK(full.ensure((size_t)link_bytes_per_site_dir(I.p, 18) * 4 * V));
+        launch_pack_links(I.p, 18, c->g, links_dev, full.p, c->st);
+        OV_TRY(launched(c));
+        std::swap(I.links, full);
+        OV_CK(cudaStreamSynchronize(c->st));
+        full.release();
+      }
+      return OV_OK;
+    }
+    return fail(c, OV_ERR_INVALID, "OV_STENCIL must be \"tpb,minb,lrec\" with tpb in 32..256 (multiple of 32), "
+                                   "minb in 2..4, lrec 12 or 18");
+  }
+  if (V < 4096) return OV_OK;  // tiny lattices: launch overhead dominates
+  OV_TRY(ensure_work(c, I, 1));
+  const size_t pb = I.pbytes(V);
+  for (DevBuf* b : {&I.perp, &I.t, &I.bA, &I.bB}) OV_CK(cudaMemsetAsync(b->p, 0, pb, c->st));
+  DevBuf alt;  // the other 16-bit link layout
+  if (is16) {
+    OV_CK(alt.ensure((size_t)link_bytes_per_site_dir(I.p, 18) * 4 * V));
+    launch_pack_links(I.p, 18, c->g, links_dev, alt.p, c->st);
+    OV_TRY(launched(c));
+  }
+  cudaEvent_t e0, e1;
+  OV_CK(cudaEventCreate(&e0));
+  OV_CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  DslashCfg best_cfg = I.cfg;
+  const int tpbs[] = {128, 192, 256};
+  const int minbs[] = {2, 3, 4};
+  const int lrecs[] = {12, 18};
+  for (int lrec : lrecs) {
+    if (!is16 && lrec == 18) continue;
+    const void* links = (lrec == 18 && is16) ? alt.p : I.links.p;
+    for (int tpb : tpbs)
+      for (int minb : minbs) {
+        DslashCfg cfg{tpb, minb, is16 ? lrec : 12};
+        EpiArgs ek;
+        ek.m_w = c->m_w;
+        EpiArgs er = ek;
+        er.v[0] = I.bA.p;
+        er.w[0] = 0.5;
+        er.v[1] = I.bB.p;
+        er.w[1] = -1.0;
+        er.v[2] = I.perp.p;
+        er.w[2] = 0.25;
+        for (int rep = 0; rep < 2; ++rep) {  // warm-up then timed
+          if (rep == 1) OV_CK(cudaEventRecord(e0, c->st));
+          for (int k = 0; k < 3; ++k) {
+            launch_dslash(I.p, I.p, cfg, c->g, links, I.perp.p, I.t.p, ek, 1, c->st);
+            launch_dslash(I.p, I.p, cfg, c->g, links, I.t.p, I.bB.p, er, 1, c->st);
+          }
+          OV_TRY(launched(c, 6));
+        }
+        OV_CK(cudaEventRecord(e1, c->st));
+        OV_CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        OV_CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          best_cfg = cfg;
+        }
+      }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  I.cfg = best_cfg;
+  if (is16 && best_cfg.lrec == 18) std::swap(I.links, alt);
+  alt.release();
+  return OV_OK;
+}
+
 ov_status init_inst(ov_ctx* c, Inst& I, OpPrec p, const void* links_dev) {
   I.p = p;
   I.pv = (p == OP_F64) ? OP_F64 : OP_F32;
   I.active = true;
-  OV_CK(I.links.ensure((size_t)link_bytes_per_site_dir(p) * 4 * c->g.V));
-  launch_pack_links(p, c->g, links_dev, I.links.p, c->st);
-  return launched(c);
+  OV_CK(I.links.ensure((size_t)link_bytes_per_site_dir(p, 12) * 4 * c->g.V));
+  launch_pack_links(p, 12, c->g, links_dev, I.links.p, c->st);
+  OV_TRY(launched(c));
+  return autotune(c, I, links_dev);
 }
 
 }  // namespace ov
@@ -468,7 +557,7 @@ static ov_status apply_stencil(ov_ctx* c, const void* in, void* out, int nrhs, o
   EpiArgs e;
   e.wilson = wilson;
   e.m_w = c->m_w;
-  OV_TRY(dslash(c, I.p, I.pv, I.links.p, src, I.xout.p, e, nrhs));
+  OV_TRY(dslash(c, I, I.pv, src, I.xout.p, e, nrhs));
   return unpack_output(c, I, I.xout.p, out, nrhs, dt);
 }
 
@@ -653,6 +742,11 @@ ov_status ov_solve(ov_ctx* c, double mu, double tol, int maxit, const void* b, v
 ov_status ov_get_stats(const ov_ctx* c, ov_stats* out) {
   if (!c || !out) return OV_ERR_INVALID;
   *out = c->stats;
+  const Inst& I = (c->prec == OV_FP64) ? c->hi : c->lo;
+  out->stencil_tpb = I.cfg.tpb;
+  out->stencil_minb = I.cfg.minb;
+  out->stencil_lrec = (I.p == OP_F64) ? 18 : I.cfg.lrec;
+  out->reserved = 0;
   return OV_OK;
 }
 

@@ -122,9 +122,9 @@ void launch_unpack_spinor(OpPrec p, IfaceType it, const LatticeH& g, const void*
   });
 }
 
-template <class T>
-__global__ void k_pack_links(const double2* __restrict__ in, void* __restrict__ out, int64_t V) {
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+template <class T, int LREC>
+__global__ void k_pack_links(const double2* __restrict__ in, void* __restrict__ out, int V) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
   const int mu = blockIdx.y;
   const double2* u = in + ((int64_t)mu * V + s) * 9;
@@ -137,6 +137,15 @@ __global__ void k_pack_links(const double2* __restrict__ in, void* __restrict__ 
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       q[c * V + s] = make_float4((float)u[2 * c].x, (float)u[2 * c].y, (float)u[2 * c + 1].x, (float)u[2 * c + 1].y);
+  } else if constexpr (LREC == 18) {
+    uint2* q = static_cast<uint2*>(out) + (int64_t)mu * 5 * V;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      uint2 v;
+      v.x = pack2<T>((float)u[2 * c].x, (float)u[2 * c].y);
+      v.y = (c < 4) ? pack2<T>((float)u[2 * c + 1].x, (float)u[2 * c + 1].y) : 0u;
+      q[c * V + s] = v;
+    }
   } else {
     uint2* q = static_cast<uint2*>(out) + (int64_t)mu * 3 * V;
 #pragma unroll
@@ -149,9 +158,22 @@ __global__ void k_pack_links(const double2* __restrict__ in, void* __restrict__ 
   }
 }
 
-void launch_pack_links(OpPrec p, const LatticeH& g, const void* in, void* out, cudaStream_t st) {
+void launch_pack_links(OpPrec p, int lrec, const LatticeH& g, const void* in, void* out, cudaStream_t st) {
   dim3 grid(grid_for(g.V), 4);
-  OV_DISPATCH1(p, T, { k_pack_links<T><<<grid, kThreads, 0, st>>>(static_cast<const double2*>(in), out, g.V); });
+  const double2* src = static_cast<const double2*>(in);
+  const int V = (int)g.V;
+  switch (p) {
+    case OP_F64: k_pack_links<F64, 18><<<grid, kThreads, 0, st>>>(src, out, V); break;
+    case OP_F32: k_pack_links<F32, 12><<<grid, kThreads, 0, st>>>(src, out, V); break;
+    case OP_F16:
+      if (lrec == 18) k_pack_links<F16, 18><<<grid, kThreads, 0, st>>>(src, out, V);
+      else k_pack_links<F16, 12><<<grid, kThreads, 0, st>>>(src, out, V);
+      break;
+    case OP_B16:
+      if (lrec == 18) k_pack_links<B16, 18><<<grid, kThreads, 0, st>>>(src, out, V);
+      else k_pack_links<B16, 12><<<grid, kThreads, 0, st>>>(src, out, V);
+      break;
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -14,6 +14,7 @@
 // Row 2 of a reconstruct-12 link is conj(row0 x row1), exact for SU(3).
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -122,12 +123,12 @@ template <> __device__ __forceinline__ uint32_t pack2<B16>(float a, float b) {
 // spinor load / store (one site of one right-hand side; p points at chunk 0)
 
 template <class T, class R>
-__device__ __forceinline__ void load_spinor(const void* p, int64_t s, int64_t V, Spinor<R>& o);
+__device__ __forceinline__ void load_spinor(const void* p, int s, int V, Spinor<R>& o);
 template <class T, class R>
-__device__ __forceinline__ void store_spinor(void* p, int64_t s, int64_t V, const Spinor<R>& o);
+__device__ __forceinline__ void store_spinor(void* p, int s, int V, const Spinor<R>& o);
 
 template <>
-__device__ __forceinline__ void load_spinor<F64, double>(const void* p, int64_t s, int64_t V, Spinor<double>& o) {
+__device__ __forceinline__ void load_spinor<F64, double>(const void* p, int s, int V, Spinor<double>& o) {
   const double2* q = static_cast<const double2*>(p);
 #pragma unroll
   for (int c = 0; c < 12; ++c) {
@@ -136,13 +137,13 @@ __device__ __forceinline__ void load_spinor<F64, double>(const void* p, int64_t 
   }
 }
 template <>
-__device__ __forceinline__ void store_spinor<F64, double>(void* p, int64_t s, int64_t V, const Spinor<double>& o) {
+__device__ __forceinline__ void store_spinor<F64, double>(void* p, int s, int V, const Spinor<double>& o) {
   double2* q = static_cast<double2*>(p);
 #pragma unroll
   for (int c = 0; c < 12; ++c) q[c * V + s] = make_double2(o.c[c].re, o.c[c].im);
 }
 template <>
-__device__ __forceinline__ void load_spinor<F32, float>(const void* p, int64_t s, int64_t V, Spinor<float>& o) {
+__device__ __forceinline__ void load_spinor<F32, float>(const void* p, int s, int V, Spinor<float>& o) {
   const float4* q = static_cast<const float4*>(p);
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
@@ -152,14 +153,14 @@ __device__ __forceinline__ void load_spinor<F32, float>(const void* p, int64_t s
   }
 }
 template <>
-__device__ __forceinline__ void store_spinor<F32, float>(void* p, int64_t s, int64_t V, const Spinor<float>& o) {
+__device__ __forceinline__ void store_spinor<F32, float>(void* p, int s, int V, const Spinor<float>& o) {
   float4* q = static_cast<float4*>(p);
 #pragma unroll
   for (int c = 0; c < 6; ++c)
     q[c * V + s] = make_float4(o.c[2 * c].re, o.c[2 * c].im, o.c[2 * c + 1].re, o.c[2 * c + 1].im);
 }
 template <class T>
-__device__ __forceinline__ void load_spinor16(const void* p, int64_t s, int64_t V, Spinor<float>& o) {
+__device__ __forceinline__ void load_spinor16(const void* p, int s, int V, Spinor<float>& o) {
   const uint4* q = static_cast<const uint4*>(p);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -172,7 +173,7 @@ __device__ __forceinline__ void load_spinor16(const void* p, int64_t s, int64_t 
   }
 }
 template <class T>
-__device__ __forceinline__ void store_spinor16(void* p, int64_t s, int64_t V, const Spinor<float>& o) {
+__device__ __forceinline__ void store_spinor16(void* p, int s, int V, const Spinor<float>& o) {
   uint4* q = static_cast<uint4*>(p);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -185,32 +186,32 @@ __device__ __forceinline__ void store_spinor16(void* p, int64_t s, int64_t V, co
   }
 }
 template <>
-__device__ __forceinline__ void load_spinor<F16, float>(const void* p, int64_t s, int64_t V, Spinor<float>& o) {
+__device__ __forceinline__ void load_spinor<F16, float>(const void* p, int s, int V, Spinor<float>& o) {
   load_spinor16<F16>(p, s, V, o);
 }
 template <>
-__device__ __forceinline__ void store_spinor<F16, float>(void* p, int64_t s, int64_t V, const Spinor<float>& o) {
+__device__ __forceinline__ void store_spinor<F16, float>(void* p, int s, int V, const Spinor<float>& o) {
   store_spinor16<F16>(p, s, V, o);
 }
 template <>
-__device__ __forceinline__ void load_spinor<B16, float>(const void* p, int64_t s, int64_t V, Spinor<float>& o) {
+__device__ __forceinline__ void load_spinor<B16, float>(const void* p, int s, int V, Spinor<float>& o) {
   load_spinor16<B16>(p, s, V, o);
 }
 template <>
-__device__ __forceinline__ void store_spinor<B16, float>(void* p, int64_t s, int64_t V, const Spinor<float>& o) {
+__device__ __forceinline__ void store_spinor<B16, float>(void* p, int s, int V, const Spinor<float>& o) {
   store_spinor16<B16>(p, s, V, o);
 }
 
 // Loading a spinor stored in type T into a different arithmetic type R.
 template <class T, class R>
-__device__ __forceinline__ void load_spinor_as(const void* p, int64_t s, int64_t V, Spinor<R>& o) {
+__device__ __forceinline__ void load_spinor_as(const void* p, int s, int V, Spinor<R>& o) {
   Spinor<typename Store<T>::R> tmp;
   load_spinor<T, typename Store<T>::R>(p, s, V, tmp);
 #pragma unroll
   for (int k = 0; k < 12; ++k) o.c[k] = {R(tmp.c[k].re), R(tmp.c[k].im)};
 }
 template <class T, class R>
-__device__ __forceinline__ void store_spinor_as(void* p, int64_t s, int64_t V, const Spinor<R>& o) {
+__device__ __forceinline__ void store_spinor_as(void* p, int s, int V, const Spinor<R>& o) {
   using RT = typename Store<T>::R;
   Spinor<RT> tmp;
 #pragma unroll
@@ -230,11 +231,11 @@ __device__ __forceinline__ void reconstruct_row2(SU3<R>& u) {
 }
 
 template <class T, class R>
-__device__ __forceinline__ void load_link(const void* p, int mu, int64_t s, int64_t V, SU3<R>& u);
+__device__ __forceinline__ void load_link(const void* p, int mu, int s, int V, SU3<R>& u);
 
 template <>
-__device__ __forceinline__ void load_link<F64, double>(const void* p, int mu, int64_t s, int64_t V, SU3<double>& u) {
-  const double2* q = static_cast<const double2*>(p) + (int64_t)mu * 9 * V;
+__device__ __forceinline__ void load_link<F64, double>(const void* p, int mu, int s, int V, SU3<double>& u) {
+  const double2* q = static_cast<const double2*>(p) + mu * 9 * V;
 #pragma unroll
   for (int e = 0; e < 9; ++e) {
     double2 v = __ldg(q + e * V + s);
@@ -242,8 +243,8 @@ __device__ __forceinline__ void load_link<F64, double>(const void* p, int mu, in
   }
 }
 template <>
-__device__ __forceinline__ void load_link<F32, float>(const void* p, int mu, int64_t s, int64_t V, SU3<float>& u) {
-  const float4* q = static_cast<const float4*>(p) + (int64_t)mu * 3 * V;
+__device__ __forceinline__ void load_link<F32, float>(const void* p, int mu, int s, int V, SU3<float>& u) {
+  const float4* q = static_cast<const float4*>(p) + mu * 3 * V;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     float4 v = __ldg(q + c * V + s);
@@ -253,8 +254,8 @@ __device__ __forceinline__ void load_link<F32, float>(const void* p, int mu, int
   reconstruct_row2(u);
 }
 template <class T>
-__device__ __forceinline__ void load_link16(const void* p, int mu, int64_t s, int64_t V, SU3<float>& u) {
-  const uint2* q = static_cast<const uint2*>(p) + (int64_t)mu * 3 * V;
+__device__ __forceinline__ void load_link16(const void* p, int mu, int s, int V, SU3<float>& u) {
+  const uint2* q = static_cast<const uint2*>(p) + mu * 3 * V;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     uint2 v = __ldg(q + c * V + s);
@@ -264,12 +265,29 @@ __device__ __forceinline__ void load_link16(const void* p, int mu, int64_t s, in
   }
   reconstruct_row2(u);
 }
+// 16-bit links with all 9 entries (no reconstruction): 5 uint2 chunks per
+// direction at [(mu*5 + c)*V + s], the second half of chunk 4 unused.
+template <class T>
+__device__ __forceinline__ void load_link16_full(const void* p, int mu, int s, int V, SU3<float>& u) {
+  const uint2* q = static_cast<const uint2*>(p) + mu * 5 * V;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    uint2 v = __ldg(q + c * V + s);
+    float2 a = unpack2<T>(v.x), b = unpack2<T>(v.y);
+    u.u[2 * c] = {a.x, a.y};
+    u.u[2 * c + 1] = {b.x, b.y};
+  }
+  uint2 v = __ldg(q + 4 * V + s);
+  float2 a = unpack2<T>(v.x);
+  u.u[8] = {a.x, a.y};
+}
+
 template <>
-__device__ __forceinline__ void load_link<F16, float>(const void* p, int mu, int64_t s, int64_t V, SU3<float>& u) {
+__device__ __forceinline__ void load_link<F16, float>(const void* p, int mu, int s, int V, SU3<float>& u) {
   load_link16<F16>(p, mu, s, V, u);
 }
 template <>
-__device__ __forceinline__ void load_link<B16, float>(const void* p, int mu, int64_t s, int64_t V, SU3<float>& u) {
+__device__ __forceinline__ void load_link<B16, float>(const void* p, int mu, int s, int V, SU3<float>& u) {
   load_link16<B16>(p, mu, s, V, u);
 }
 

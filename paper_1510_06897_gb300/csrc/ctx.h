@@ -37,6 +37,7 @@ struct Inst {
   OpPrec p = OP_F64;   // link / recurrence storage
   OpPrec pv = OP_F64;  // vector storage: deflation, assembly, solver vectors
   bool active = false;
+  DslashCfg cfg;  // stencil launch shape / link layout (autotuned)
   DevBuf links, evecs;
   DevBuf xin, xout, d, tmp;          // pv
   DevBuf perp, t, bA, bB;            // p
@@ -103,9 +104,8 @@ std::vector<double> chebyshev_coefficients(int order, double a, double b);
 ov_status pack_input(ov_ctx* c, Inst& I, const void* in, int nrhs, ov_dtype dt, void* dst);
 ov_status unpack_output(ov_ctx* c, Inst& I, const void* src, void* out, int nrhs, ov_dtype dt);
 ov_status check_dtype(ov_ctx* c, int nrhs, ov_dtype dt);
-// launch the stencil (counted, profiled when enabled)
-ov_status dslash(ov_ctx* c, OpPrec p, OpPrec out_prec, const void* links, const void* in, void* out,
-                 const EpiArgs& e, int nrhs);
+// launch the stencil of instance I (counted, profiled when enabled)
+ov_status dslash(ov_ctx* c, Inst& I, OpPrec out_prec, const void* in, void* out, const EpiArgs& e, int nrhs);
 // fold completed profiling event pairs into the stats (call after a stream sync)
 void prof_collect(ov_ctx* c);
 // out (storage I.p) = stencil epilogue of K applied to `in` (see EpiArgs)

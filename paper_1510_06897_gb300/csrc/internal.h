@@ -14,8 +14,8 @@ inline int spinor_bytes_per_site(OpPrec p) {
   return p == OP_F64 ? 192 : p == OP_F32 ? 96 : 48;
 }
 // bytes of one direction's link at one site as stored
-inline int link_bytes_per_site_dir(OpPrec p) {
-  return p == OP_F64 ? 144 : p == OP_F32 ? 48 : 24;
+inline int link_bytes_per_site_dir(OpPrec p, int lrec = 12) {
+  return p == OP_F64 ? 144 : p == OP_F32 ? 48 : (lrec == 18 ? 40 : 24);
 }
 
 struct LatticeH {
@@ -44,8 +44,18 @@ struct EpiArgs {
   double c0 = 0.0;
 };
 
-void launch_dslash(OpPrec p, OpPrec out_prec, const LatticeH& g, const void* links, const void* in, void* out,
-                   const EpiArgs& e, int nrhs, cudaStream_t st);
+// Launch shape and link layout of the stencil (chosen per operator by the
+// autotuner): threads per block over an (x, y) plane, a register cap (minb
+// 2 / 3 / 4 = at most 128 / 85 / 64 registers), and for 16-bit links 12 (rows 0, 1; row 2 rebuilt)
+// or 18 stored reals.
+struct DslashCfg {
+  int tpb = 128;
+  int minb = 2;
+  int lrec = 12;
+};
+
+void launch_dslash(OpPrec p, OpPrec out_prec, const DslashCfg& cfg, const LatticeH& g, const void* links,
+                   const void* in, void* out, const EpiArgs& e, int nrhs, cudaStream_t st);
 
 // ---- vector kernels (blas.cu) ---------------------------------------------
 // Interface formats: complex128 / complex64 AoS [nrhs][V][4][3].
@@ -57,8 +67,9 @@ void launch_pack_spinor(OpPrec p, IfaceType it, const LatticeH& g, const void* i
 // interface <- internal
 void launch_unpack_spinor(OpPrec p, IfaceType it, const LatticeH& g, const void* in, void* out, int nrhs,
                           double scale, cudaStream_t st);
-// links complex128 [4][V][3][3] -> internal storage
-void launch_pack_links(OpPrec p, const LatticeH& g, const void* in, void* out, cudaStream_t st);
+// links complex128 [4][V][3][3] -> internal storage (lrec 12 or 18 reals for
+// 16-bit storage; FP64 always 18, FP32 always 12)
+void launch_pack_links(OpPrec p, int lrec, const LatticeH& g, const void* in, void* out, cudaStream_t st);
 
 // Number of blocks every reduction kernel uses (fixed, so that results are
 // bitwise reproducible).
