@@ -177,8 +177,29 @@ ov_status ov_set_profiling(ov_ctx* ctx, int on);
 ov_status ov_get_stats(const ov_ctx* ctx, ov_stats* out);
 ov_status ov_reset_stats(ov_ctx* ctx);
 
+/* No counterpart in the paper.  D_W in (Eq. 2 operator, FP64 arithmetic, as
+ * ov_wilson on an OV_FP64 context) for callers that cannot allocate device
+ * memory at all: code embedded in a framework whose memory pool owns the
+ * whole GPU, or a latency-critical loop where a cudaMalloc may block or fail.
+ * No context is needed and nothing is allocated: the packed copies of links
+ * and spinors go to one file-scope device array of 32 MiB, present on every
+ * GPU that loads this library until the process exits.  Requirements:
+ * V * (576 + 384 * nrhs) <= 32 MiB (e.g. V <= 34952 sites for one RHS), else
+ * OV_ERR_INVALID; links (complex128 [4][V][3][3]), in and out (dtype
+ * [nrhs][V][4][3]) in device memory, else OV_ERR_INVALID.  Work is issued on
+ * cuda_stream (NULL = legacy default stream) and the call returns when it is
+ * complete.  All calls share the array, which keeps the last call's contents
+ * (each call writes everything it reads, so nothing needs clearing): calls
+ * that may overlap on the GPU race and must be serialised by the caller.  The
+ * first call on a device looks up the array's address with that device
+ * current and caches it; make that first call before any stream capture.
+ * Error text: ov_last_error(NULL). */
+ov_status ov_wilson_noalloc(const int dims[4], const void* links, const void* in, void* out, int nrhs,
+                            ov_dtype dtype, int antiperiodic_t, void* cuda_stream);
+
 /* Last error message of the context ("" if none); never NULL.  Passing NULL
- * returns the message of the last failed ov_create on this thread. */
+ * returns the message of the last failed ov_create or ov_wilson_noalloc call
+ * on this thread. */
 const char* ov_last_error(const ov_ctx* ctx);
 
 #ifdef __cplusplus

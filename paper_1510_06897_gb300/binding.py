@@ -68,6 +68,7 @@ _SIGNATURES = {
     "ov_get_stats": [_vp, ctypes.POINTER(ov_stats)],
     "ov_reset_stats": [_vp],
     "ov_set_profiling": [_vp, _i],
+    "ov_wilson_noalloc": [ctypes.POINTER(_i), _vp, _vp, _vp, _i, _i, _i, _vp],
 }
 
 
@@ -210,6 +211,13 @@ def ov_get_stats(ctx):
     s = ov_stats()
     _check(lib().ov_get_stats(ctx, ctypes.byref(s)), ctx)
     return {name: getattr(s, name) for name, _ in ov_stats._fields_}
+
+
+def ov_wilson_noalloc(dims, links, inp, out, nrhs, antiperiodic_t=False, stream=None):
+    """D_W without a context and without any device allocation (see overlap.h)."""
+    cdims = (_i * 4)(*[int(d) for d in dims])
+    return _check(lib().ov_wilson_noalloc(cdims, _ptr(links), _ptr(inp), _ptr(out), int(nrhs), _dtype_code(inp),
+                                          int(bool(antiperiodic_t)), _stream_ptr(stream)), None)
 
 
 def ov_set_profiling(ctx, on):

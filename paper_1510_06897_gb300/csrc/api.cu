@@ -20,6 +20,11 @@ thread_local std::string g_create_error;
 }  // namespace
 
 namespace ov {
+// Message returned by ov_last_error(NULL) on this thread (context-free calls).
+void set_thread_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace ov
+
+namespace ov {
 
 ov_status fail(ov_ctx* c, ov_status s, const std::string& msg) {
   if (c) c->err = msg;
