@@ -79,6 +79,7 @@ def ncu_traffic(prec):
     if f"source_sha256_16: {sha}" not in text:
         return None
     for line in text.splitlines():
+        line = line.strip()
         if line.startswith(f"traffic_bytes_per_site_{prec}:"):
             return float(line.split(":")[1])
     return None
