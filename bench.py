@@ -69,7 +69,7 @@ def measured_peaks():
 def ncu_traffic(prec):
     """DRAM bytes per site per stencil launch from the committed ncu summary,
     if it was taken on the current stencil source (else None)."""
-    src = os.path.join(ROOT, "paper_1510_06897_gb300", "csrc", "dslash.cu")
+    src = os.path.join(ROOT, "paper_1510_06897_gb300", "csrc", "dslash_kernel.cuh")
     path = os.path.join(ROOT, "profiles", "dslash_24x24x24x48.md")
     try:
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]

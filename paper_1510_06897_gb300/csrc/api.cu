@@ -92,7 +92,11 @@ void prof_collect(ov_ctx* c) {
   c->ev_used = 0;
 }
 
+ov_status batch_cfg(ov_ctx* c, Inst& I, int nrhs, DslashCfg* out);
+
 ov_status dslash(ov_ctx* c, Inst& I, OpPrec out_prec, const void* in, void* out, const EpiArgs& e, int nrhs) {
+  DslashCfg cfg;
+  OV_TRY(batch_cfg(c, I, nrhs, &cfg));
   if (c->prof) {
     while (c->evs.size() < c->ev_used + 2) {
       cudaEvent_t ev;
@@ -101,7 +105,8 @@ ov_status dslash(ov_ctx* c, Inst& I, OpPrec out_prec, const void* in, void* out,
     }
     OV_CK(cudaEventRecord(c->evs[c->ev_used], c->st));
   }
-  launch_dslash(I.p, out_prec, I.cfg, c->g, I.links.p, in, out, e, nrhs, c->st);
+  if (!launch_dslash(I.p, out_prec, cfg, c->g, I.links.p, in, out, e, nrhs, c->st))
+    return fail(c, OV_ERR_CUDA, "stencil variant not compiled");
   c->stats.dslash_launches++;
   ov_status s = launched(c);
   if (s != OV_OK) return s;
@@ -192,17 +197,28 @@ ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kin
   const int n_ev = c->n_ev;
 
   // S3: deflation projection c_i = phi_i^dagger psi, psi_perp = psi - sum c_i phi_i,
-  //     d = sum sgn(lambda_i) c_i phi_i  (both scaled by `scale`)
+  //     d = sum sgn(lambda_i) c_i phi_i  (both scaled by `scale`).  Several
+  //     right-hand sides: one Gram launch reads every eigenvector once for all
+  //     of them (c stored [i][r]); one right-hand side: the projection kernel.
+  const bool batched = (n_ev > 0 && nrhs > 1 && n_ev <= gram_max_vectors() && nrhs <= gram_max_vectors());
+  if (batched) {
+    OV_CK(c->d_gram.ensure(sizeof(double2) * (size_t)n_ev * nrhs * kReduceBlocks));
+    OV_CK(launch_gram(I.pv, I.evecs.p, n_ev, in, nrhs, V, c->d_gram.as<double2>(), kReduceBlocks, c->st, g5in));
+    OV_TRY(launched(c));
+    launch_reduce_partials(c->d_gram.as<double2>(), n_ev * nrhs, kReduceBlocks, c->d_c.as<double2>(), c->st);
+    OV_TRY(launched(c));
+  }
   for (int r = 0; r < nrhs; ++r) {
     const char* in_r = static_cast<const char*>(in) + r * vb;
-    double2* cr = c->d_c.as<double2>() + (size_t)r * std::max(1, n_ev);
-    if (n_ev > 0) {
+    double2* cr = batched ? c->d_c.as<double2>() + r : c->d_c.as<double2>() + (size_t)r * std::max(1, n_ev);
+    const int cstride = batched ? nrhs : 1;
+    if (n_ev > 0 && !batched) {
       launch_defl_dot(I.pv, c->g, I.evecs.p, n_ev, in_r, g5in, c->d_partial.as<double2>(), c->st);
       OV_TRY(launched(c));
       launch_reduce_partials(c->d_partial.as<double2>(), n_ev, kReduceBlocks, cr, c->st);
       OV_TRY(launched(c));
     }
-    launch_defl_combine(I.pv, I.p, c->g, I.evecs.p, n_ev, cr, c->d_sgn.as<double>(), in_r, g5in, scale,
+    launch_defl_combine(I.pv, I.p, c->g, I.evecs.p, n_ev, cr, cstride, c->d_sgn.as<double>(), in_r, g5in, scale,
                         I.perp.c() + r * pb, n_ev > 0 ? I.d.c() + r * vb : nullptr, c->st);
     OV_TRY(launched(c));
   }
@@ -372,90 +388,163 @@ ov_status unpack_output(ov_ctx* c, Inst& I, const void* src, void* out, int nrhs
   return finish_out(c, out, bytes, staged);
 }
 
-// Times the stencil variants (threads per block, register cap, and for 16-bit
-// links the 12- or 18-real layout) on this lattice with a plain K step and a
-// recurrence step, and keeps the fastest.
-// The environment variable OV_STENCIL="tpb,minb,lrec" (e.g. "192,3,12")
+// Times one stencil variant on nrhs right-hand sides: a K step and a
+// recurrence step (three extra vector reads), after one warm-up pair.
+ov_status time_variant(ov_ctx* c, Inst& I, const DslashCfg& cfg, const void* links, int nrhs, DevBuf* buf,
+                       cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+  EpiArgs ek;
+  ek.m_w = c->m_w;
+  EpiArgs er = ek;
+  er.v[0] = buf[2].p;
+  er.w[0] = 0.5;
+  er.v[1] = buf[3].p;
+  er.w[1] = -1.0;
+  er.v[2] = buf[0].p;
+  er.w[2] = 0.25;
+  for (int rep = 0; rep < 2; ++rep) {
+    if (rep == 1) OV_CK(cudaEventRecord(e0, c->st));
+    for (int k = 0; k < (nrhs > 4 ? 1 : 3); ++k) {
+      if (!launch_dslash(I.p, I.p, cfg, c->g, links, buf[0].p, buf[1].p, ek, nrhs, c->st) ||
+          !launch_dslash(I.p, I.p, cfg, c->g, links, buf[1].p, buf[3].p, er, nrhs, c->st))
+        return fail(c, OV_ERR_CUDA, "stencil variant not compiled");
+    }
+    OV_TRY(launched(c, 2));
+  }
+  OV_CK(cudaEventRecord(e1, c->st));
+  OV_CK(cudaEventSynchronize(e1));
+  OV_CK(cudaEventElapsedTime(ms, e0, e1));
+  return OV_OK;
+}
+
+// (minb, rt) pairs compiled for the stencil (see dslash_kernel.cuh).
+const int kVariants[][2] = {{2, 1}, {3, 1}, {4, 1}, {2, 2}, {3, 2}, {1, 4}, {2, 4}};
+
+// The environment variable OV_STENCIL="tpb,minb,lrec[,rt]" (e.g. "192,3,12")
 // skips the timing and pins one variant (used for reproducible profiles).
+bool pinned_cfg(DslashCfg* cfg, bool* bad) {
+  *bad = false;
+  const char* env = std::getenv("OV_STENCIL");
+  if (!env) return false;
+  int tpb = 0, minb = 0, lrec = 0, rt = 1;
+  const int n = std::sscanf(env, "%d,%d,%d,%d", &tpb, &minb, &lrec, &rt);
+  bool ok = n >= 3 && tpb >= 32 && tpb <= 256 && tpb % 32 == 0 && (lrec == 12 || lrec == 18);
+  bool listed = false;
+  for (const auto& v : kVariants) listed = listed || (v[0] == minb && v[1] == rt);
+  if (!ok || !listed) {
+    *bad = true;
+    return false;
+  }
+  *cfg = DslashCfg{tpb, minb, lrec, rt};
+  return true;
+}
+
+// Times the one-RHS stencil variants (threads per block, register cap, and
+// for 16-bit links the 12- or 18-real layout) on this lattice and keeps the
+// fastest; the link layout chosen here is kept for every nrhs.
 ov_status autotune(ov_ctx* c, Inst& I, const void* links_dev) {
   const int64_t V = c->g.V;
   I.cfg = DslashCfg{};
+  I.cfg_batch.clear();
   const bool is16 = (I.p == OP_F16 || I.p == OP_B16);
-  if (const char* env = std::getenv("OV_STENCIL")) {
-    int tpb = 0, minb = 0, lrec = 0;
-    if (std::sscanf(env, "%d,%d,%d", &tpb, &minb, &lrec) == 3 && tpb >= 32 && tpb <= 256 && tpb % 32 == 0 &&
-        minb >= 2 && minb <= 4 && (lrec == 12 || lrec == 18)) {
-      I.cfg = DslashCfg{tpb, minb, is16 ? lrec : 12};
-      if (is16 && lrec == 18) {
-        DevBuf full;
-        OV_CK(full.ensure((size_t)link_bytes_per_site_dir(I.p, 18) * 4 * V));
-        launch_pack_links(I.p, 18, c->g, links_dev, full.p, c->st);
-        OV_TRY(launched(c));
-        std::swap(I.links, full);
-        OV_CK(cudaStreamSynchronize(c->st));
-        full.release();
-      }
-      return OV_OK;
-    }
-    return fail(c, OV_ERR_INVALID, "OV_STENCIL must be \"tpb,minb,lrec\" with tpb in 32..256 (multiple of 32), "
-                                   "minb in 2..4, lrec 12 or 18");
-  }
-  if (V < 4096) return OV_OK;  // tiny lattices: launch overhead dominates
-  OV_TRY(ensure_work(c, I, 1));
-  const size_t pb = I.pbytes(V);
-  for (DevBuf* b : {&I.perp, &I.t, &I.bA, &I.bB}) OV_CK(cudaMemsetAsync(b->p, 0, pb, c->st));
+  DslashCfg pin;
+  bool bad = false;
+  const bool pinned = pinned_cfg(&pin, &bad);
+  if (bad)
+    return fail(c, OV_ERR_INVALID, "OV_STENCIL must be \"tpb,minb,lrec[,rt]\" naming a compiled variant");
   DevBuf alt;  // the other 16-bit link layout
-  if (is16) {
+  if (is16 && (!pinned || pin.lrec == 18)) {
     OV_CK(alt.ensure((size_t)link_bytes_per_site_dir(I.p, 18) * 4 * V));
     launch_pack_links(I.p, 18, c->g, links_dev, alt.p, c->st);
     OV_TRY(launched(c));
   }
-  cudaEvent_t e0, e1;
-  OV_CK(cudaEventCreate(&e0));
-  OV_CK(cudaEventCreate(&e1));
-  float best = 1e30f;
-  DslashCfg best_cfg = I.cfg;
-  const int tpbs[] = {128, 192, 256};
-  const int minbs[] = {2, 3, 4};
-  const int lrecs[] = {12, 18};
-  for (int lrec : lrecs) {
-    if (!is16 && lrec == 18) continue;
-    const void* links = (lrec == 18 && is16) ? alt.p : I.links.p;
-    for (int tpb : tpbs)
-      for (int minb : minbs) {
-        DslashCfg cfg{tpb, minb, is16 ? lrec : 12};
-        EpiArgs ek;
-        ek.m_w = c->m_w;
-        EpiArgs er = ek;
-        er.v[0] = I.bA.p;
-        er.w[0] = 0.5;
-        er.v[1] = I.bB.p;
-        er.w[1] = -1.0;
-        er.v[2] = I.perp.p;
-        er.w[2] = 0.25;
-        for (int rep = 0; rep < 2; ++rep) {  // warm-up then timed
-          if (rep == 1) OV_CK(cudaEventRecord(e0, c->st));
-          for (int k = 0; k < 3; ++k) {
-            launch_dslash(I.p, I.p, cfg, c->g, links, I.perp.p, I.t.p, ek, 1, c->st);
-            launch_dslash(I.p, I.p, cfg, c->g, links, I.t.p, I.bB.p, er, 1, c->st);
+  DslashCfg best_cfg;
+  if (pinned) {
+    best_cfg = DslashCfg{pin.tpb, pin.minb, is16 ? pin.lrec : 12, 1};
+    if (I.p == OP_F64 && pin.rt != 1) best_cfg.rt = 1;
+  } else if (V >= 4096) {
+    DevBuf buf[4];
+    for (DevBuf& b : buf) {
+      OV_CK(b.ensure(I.pbytes(V)));
+      OV_CK(cudaMemsetAsync(b.p, 0, I.pbytes(V), c->st));
+    }
+    cudaEvent_t e0, e1;
+    OV_CK(cudaEventCreate(&e0));
+    OV_CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int lrec : {12, 18}) {
+      if (!is16 && lrec == 18) continue;
+      const void* links = (lrec == 18 && is16) ? alt.p : I.links.p;
+      for (int tpb : {128, 192, 256})
+        for (const auto& v : kVariants) {
+          if (v[1] != 1) continue;
+          DslashCfg cfg{tpb, v[0], is16 ? lrec : 12, 1};
+          float ms = 0.f;
+          OV_TRY(time_variant(c, I, cfg, links, 1, buf, e0, e1, &ms));
+          if (ms < best) {
+            best = ms;
+            best_cfg = cfg;
           }
-          OV_TRY(launched(c, 6));
         }
-        OV_CK(cudaEventRecord(e1, c->st));
-        OV_CK(cudaEventSynchronize(e1));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  I.cfg = best_cfg;
+  if (is16 && best_cfg.lrec == 18) std::swap(I.links, alt);
+  OV_CK(cudaStreamSynchronize(c->st));
+  alt.release();
+  return OV_OK;
+}
+
+// Stencil shape for nrhs right-hand sides: tuned on first use (threads per
+// block, register cap, right-hand sides per thread; link layout as tuned at
+// create) and cached per nrhs.
+ov_status batch_cfg(ov_ctx* c, Inst& I, int nrhs, DslashCfg* out) {
+  if (nrhs <= 1) {
+    *out = I.cfg;
+    return OV_OK;
+  }
+  for (const auto& kv : I.cfg_batch)
+    if (kv.first == nrhs) {
+      *out = kv.second;
+      return OV_OK;
+    }
+  DslashCfg best_cfg = I.cfg;
+  DslashCfg pin;
+  bool bad = false;
+  if (pinned_cfg(&pin, &bad)) {
+    best_cfg.tpb = pin.tpb;
+    best_cfg.minb = pin.minb;
+    best_cfg.rt = (I.p == OP_F64) ? 1 : pin.rt;
+    if (best_cfg.rt == 1 && best_cfg.minb == 1) best_cfg.minb = 2;
+  } else if (c->g.V >= 4096) {
+    const int64_t V = c->g.V;
+    DevBuf buf[4];
+    for (DevBuf& b : buf) {
+      OV_CK(b.ensure(I.pbytes(V) * nrhs));
+      OV_CK(cudaMemsetAsync(b.p, 0, I.pbytes(V) * nrhs, c->st));
+    }
+    cudaEvent_t e0, e1;
+    OV_CK(cudaEventCreate(&e0));
+    OV_CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int tpb : {128, 192, 256})
+      for (const auto& v : kVariants) {
+        if (v[1] > nrhs || (I.p == OP_F64 && v[1] != 1)) continue;
+        DslashCfg cfg{tpb, v[0], I.cfg.lrec, v[1]};
         float ms = 0.f;
-        OV_CK(cudaEventElapsedTime(&ms, e0, e1));
+        OV_TRY(time_variant(c, I, cfg, I.links.p, nrhs, buf, e0, e1, &ms));
         if (ms < best) {
           best = ms;
           best_cfg = cfg;
         }
       }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    OV_CK(cudaStreamSynchronize(c->st));
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  I.cfg = best_cfg;
-  if (is16 && best_cfg.lrec == 18) std::swap(I.links, alt);
-  alt.release();
+  I.cfg_batch.emplace_back(nrhs, best_cfg);
+  *out = best_cfg;
   return OV_OK;
 }
 
@@ -538,7 +627,7 @@ ov_status ov_destroy(ov_ctx* c) {
   c->hi.release();
   c->lo.release();
   for (cudaEvent_t ev : c->evs) cudaEventDestroy(ev);
-  for (DevBuf* b : {&c->d_sgn, &c->d_c, &c->d_partial, &c->d_scalars, &c->stage_in, &c->stage_out, &c->stage_links,
+  for (DevBuf* b : {&c->d_sgn, &c->d_c, &c->d_partial, &c->d_scalars, &c->d_gram, &c->stage_in, &c->stage_out, &c->stage_links,
                     &c->o_x, &c->o_r, &c->o_rhs, &c->o_q})
     b->release();
   if (c->h_scalars) cudaFreeHost(c->h_scalars);

@@ -252,7 +252,7 @@ void launch_reduce_partials(const double2* partial, int n, int nblk, double2* ou
 // TV: storage of phi_i, psi and d; TP: storage of psi_perp.
 template <class TV, class TP>
 __global__ void k_defl_combine(const char* __restrict__ evecs, int n_ev, const double2* __restrict__ c,
-                               const double* __restrict__ sgn, const char* __restrict__ psi, int64_t V, int g5,
+                               int cstride, const double* __restrict__ sgn, const char* __restrict__ psi, int64_t V, int g5,
                                double scale, char* __restrict__ psi_perp, char* __restrict__ d) {
   using R = typename Arith<TV, TV>::R;
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -269,7 +269,8 @@ __global__ void k_defl_combine(const char* __restrict__ evecs, int n_ev, const d
   for (int i = 0; i < n_ev; ++i) {
     Spinor<R> f;
     load_spinor_as<TV, R>(evecs + i * evec_bytes, s, V, f);
-    const cplx<R> ci = {R(c[i].x), R(c[i].y)};
+    const double2 cd = c[(int64_t)i * cstride];
+    const cplx<R> ci = {R(cd.x), R(cd.y)};
     const R si = R(sgn[i]);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
@@ -289,7 +290,7 @@ __global__ void k_defl_combine(const char* __restrict__ evecs, int n_ev, const d
 }
 
 void launch_defl_combine(OpPrec pv, OpPrec pp, const LatticeH& g, const void* evecs, int n_ev, const double2* c,
-                         const double* sgn, const void* psi, int g5, double scale, void* psi_perp, void* d,
+                         int cstride, const double* sgn, const void* psi, int g5, double scale, void* psi_perp, void* d,
                          cudaStream_t st) {
   const char* e = static_cast<const char*>(evecs);
   const char* x = static_cast<const char*>(psi);
@@ -297,10 +298,10 @@ void launch_defl_combine(OpPrec pv, OpPrec pp, const LatticeH& g, const void* ev
   char* dd = static_cast<char*>(d);
   const unsigned gr = grid_for(g.V);
   if (pv == OP_F64) {
-    k_defl_combine<F64, F64><<<gr, kThreads, 0, st>>>(e, n_ev, c, sgn, x, g.V, g5, scale, pp_, dd);
+    k_defl_combine<F64, F64><<<gr, kThreads, 0, st>>>(e, n_ev, c, cstride, sgn, x, g.V, g5, scale, pp_, dd);
   } else {
     OV_DISPATCH1(pp, TP, {
-      k_defl_combine<F32, TP><<<gr, kThreads, 0, st>>>(e, n_ev, c, sgn, x, g.V, g5, scale, pp_, dd);
+      k_defl_combine<F32, TP><<<gr, kThreads, 0, st>>>(e, n_ev, c, cstride, sgn, x, g.V, g5, scale, pp_, dd);
     });
   }
 }

@@ -37,7 +37,8 @@ struct Inst {
   OpPrec p = OP_F64;   // link / recurrence storage
   OpPrec pv = OP_F64;  // vector storage: deflation, assembly, solver vectors
   bool active = false;
-  DslashCfg cfg;  // stencil launch shape / link layout (autotuned)
+  DslashCfg cfg;  // stencil launch shape / link layout for one RHS (autotuned at create)
+  std::vector<std::pair<int, DslashCfg>> cfg_batch;  // tuned shapes for nrhs > 1
   DevBuf links, evecs;
   DevBuf xin, xout, d, tmp;          // pv
   DevBuf perp, t, bA, bB;            // p
@@ -69,7 +70,7 @@ struct ov_ctx {
   std::vector<double> coef;
   int n_ev = 0;
   std::vector<double> evals, sgn;
-  DevBuf d_sgn, d_c, d_partial, d_scalars;
+  DevBuf d_sgn, d_c, d_partial, d_scalars, d_gram;
   DevBuf stage_in, stage_out, stage_links;
   DevBuf o_x, o_r, o_rhs, o_q;  // FP64 outer-solver vectors
   double* h_scalars = nullptr;  // pinned

@@ -1,0 +1,253 @@
+// Stencil kernel template (shared by the per-precision translation units
+// dslash_f64.cu, dslash_f32.cu, dslash_f16.cu, dslash_b16.cu).
+//
+//   (D_W x)(s) = 4 x(s) - 1/2 sum_mu [ (1 - gamma_mu) U_mu(s) x(s+mu^)
+//                                     + (1 + gamma_mu) U_mu(s-mu^)^dagger x(s-mu^) ]     (Eq. 2)
+//   K x        = gamma5 (D_W - m_W) x                                                      (Sec. 2)
+//
+// One thread per site and right-hand side.  Each of the 8 hops projects the
+// neighbour spinor to a two-spinor with (1 -/+ gamma_mu), multiplies the two
+// colour vectors by U or U^dagger (reconstructed from 12 reals in FP32/FP16/
+// BF16 storage) and expands the result back into the accumulator, so a hop
+// costs 2 SU(3) mat-vecs instead of 4.  The paper merges the Wilson matrix with
+// the polynomial algebra of the sign function into one kernel (Sec. 2); here
+// the merge is the epilogue: out = c0 y + G(s1 r + sum_j w_j v_j), which
+// covers plain K, every step of the Chebyshev recurrence and the final
+// deflation-correction + overlap assembly (Eq. 1) without extra passes.
+//
+// Gamma basis: chiral (DeGrand-Rossi), gamma5 = diag(1, 1, -1, -1).  With
+// h = (h0, h1) the projected two-spinor, the full spinors are
+//   x:  (1-g) psi = (h0, h1,  i h1,  i h0), h = (p0 - i p3, p1 - i p2)
+//       (1+g) psi = (h0, h1, -i h1, -i h0), h = (p0 + i p3, p1 + i p2)
+//   y:  (1-g) psi = (h0, h1, -h1,  h0),     h = (p0 + p3, p1 - p2)
+//       (1+g) psi = (h0, h1,  h1, -h0),     h = (p0 - p3, p1 + p2)
+//   z:  (1-g) psi = (h0, h1,  i h0, -i h1), h = (p0 - i p2, p1 + i p3)
+//       (1+g) psi = (h0, h1, -i h0,  i h1), h = (p0 + i p2, p1 - i p3)
+//   t:  (1-g) psi = (h0, h1, -h0, -h1),     h = (p0 - p2, p1 - p3)
+//       (1+g) psi = (h0, h1,  h0,  h1),     h = (p0 + p2, p1 + p3)
+#pragma once
+#include "common.cuh"
+#include "internal.h"
+#include "spin.cuh"
+
+namespace ov {
+
+template <class LT, int LREC, class R>
+__device__ __forceinline__ void load_link_fmt(const void* p, int mu, int s, int V, SU3<R>& u) {
+  if constexpr (LREC == 18 && (std::is_same<LT, F16>::value || std::is_same<LT, B16>::value))
+    load_link16_full<LT>(p, mu, s, V, u);
+  else
+    load_link<LT, R>(p, mu, s, V, u);
+}
+
+// Both hops of direction MU for site s and the RT right-hand sides of this
+// thread (fields rhs_bytes apart, the last nv of them valid): the link of
+// each hop is loaded (and rebuilt) once and applied to every right-hand side.
+// n_f / n_b are the neighbour indices, sg_f / sg_b the boundary signs (-1
+// across an antiperiodic t boundary).
+template <int MU, class LT, int LREC, class ST, int RT, class R>
+__device__ __forceinline__ void hop_pair(int s, int n_f, int n_b, R sg_f, R sg_b, int V, const void* links,
+                                         const char* in, long long rhs_bytes, int nv, Spinor<R> (&acc)[RT]) {
+  {  // forward: (1 - gamma_mu) U_mu(s) x(s + mu^)
+    SU3<R> u;
+    load_link_fmt<LT, LREC, R>(links, MU, s, V, u);
+#pragma unroll
+    for (int r = 0; r < RT; ++r) {
+      if (r < nv) {
+        Spinor<R> p;
+        load_spinor_as<ST, R>(in + r * rhs_bytes, n_f, V, p);
+        Half<R> h, uh;
+        project<MU, -1>(p, h);
+        if (MU == 3) scale_half(h, sg_f);
+        mul_u(u, h, uh);
+        expand_add<MU, -1>(acc[r], uh);
+      }
+    }
+  }
+  {  // backward: (1 + gamma_mu) U_mu(s - mu^)^dagger x(s - mu^)
+    SU3<R> u;
+    load_link_fmt<LT, LREC, R>(links, MU, n_b, V, u);
+#pragma unroll
+    for (int r = 0; r < RT; ++r) {
+      if (r < nv) {
+        Spinor<R> p;
+        load_spinor_as<ST, R>(in + r * rhs_bytes, n_b, V, p);
+        Half<R> h, uh;
+        project<MU, +1>(p, h);
+        if (MU == 3) scale_half(h, sg_b);
+        mul_udag(u, h, uh);
+        expand_add<MU, +1>(acc[r], uh);
+      }
+    }
+  }
+}
+
+struct EpiDev {
+  int wilson, g5_out;
+  double m_w, s1, c0, wz;
+  const void* v[3];
+  double w[3];
+  const void* z;
+  const void* y;
+};
+
+struct Geo {
+  int L[4];
+  int V;
+  int LxLy;
+  int antiperiodic_t;
+};
+
+// Grid: x = sites of one (x, y) plane, y = z + Lz t slice, z = tile of RT
+// right-hand sides.  LT/LREC: link storage and 12- or 18-real layout, ST:
+// storage of the stencil input and of v[j], OT: storage of z, y and the
+// output.  MINB: minimum resident blocks of 256 threads requested from the
+// register allocator (1: no cap, 2: <= 128 registers, 3: <= 80, 4: <= 64).
+template <class LT, int LREC, class ST, class OT, int MINB, int RT>
+__global__ void __launch_bounds__(256, MINB) k_dslash(Geo g, const void* __restrict__ links,
+                                                      const char* __restrict__ in, char* out, EpiDev e,
+                                                      long long rhs_bytes, long long out_rhs_bytes, int nrhs) {
+  using R = typename Store<ST>::R;
+  const int xy = blockIdx.x * blockDim.x + threadIdx.x;
+  if (xy >= g.LxLy) return;
+  const int slice = blockIdx.y;
+  const int Lx = g.L[0], Ly = g.L[1], Lz = g.L[2], Lt = g.L[3];
+  const int y = xy / Lx, x = xy - y * Lx;
+  const int t = slice / Lz, z = slice - t * Lz;
+  const int s = slice * g.LxLy + xy;
+  const int V = g.V;
+  const int r0 = blockIdx.z * RT;
+  const int nv = min(RT, nrhs - r0);
+  const char* xin = in + (long long)r0 * rhs_bytes;
+
+  const int sz = g.LxLy, st = g.LxLy * Lz;
+  const int xp = (x == Lx - 1) ? s - (Lx - 1) : s + 1;
+  const int xm = (x == 0) ? s + (Lx - 1) : s - 1;
+  const int yp = (y == Ly - 1) ? s - (Ly - 1) * Lx : s + Lx;
+  const int ym = (y == 0) ? s + (Ly - 1) * Lx : s - Lx;
+  const int zp = (z == Lz - 1) ? s - (Lz - 1) * sz : s + sz;
+  const int zm = (z == 0) ? s + (Lz - 1) * sz : s - sz;
+  const int tp = (t == Lt - 1) ? s - (Lt - 1) * st : s + st;
+  const int tm = (t == 0) ? s + (Lt - 1) * st : s - st;
+  const R sg_tf = (g.antiperiodic_t && t == Lt - 1) ? R(-1) : R(1);
+  const R sg_tb = (g.antiperiodic_t && t == 0) ? R(-1) : R(1);
+
+  Spinor<R> acc[RT];
+#pragma unroll
+  for (int r = 0; r < RT; ++r)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[r].c[k] = {R(0), R(0)};
+  hop_pair<0, LT, LREC, ST, RT>(s, xp, xm, R(1), R(1), V, links, xin, rhs_bytes, nv, acc);
+  hop_pair<1, LT, LREC, ST, RT>(s, yp, ym, R(1), R(1), V, links, xin, rhs_bytes, nv, acc);
+  hop_pair<2, LT, LREC, ST, RT>(s, zp, zm, R(1), R(1), V, links, xin, rhs_bytes, nv, acc);
+  hop_pair<3, LT, LREC, ST, RT>(s, tp, tm, sg_tf, sg_tb, V, links, xin, rhs_bytes, nv, acc);
+
+#pragma unroll
+  for (int rr = 0; rr < RT; ++rr) {
+    if (rr >= nv) break;
+    const long long off = (long long)(r0 + rr) * rhs_bytes;
+    const long long ooff = (long long)(r0 + rr) * out_rhs_bytes;
+    Spinor<R> xs;
+    load_spinor_as<ST, R>(in + off, s, V, xs);
+    const R half = R(0.5);
+    Spinor<R> r;
+    if (e.wilson) {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) r.c[k] = R(4) * xs.c[k] - half * acc[rr].c[k];
+    } else {
+      const R diag = R(4.0 - e.m_w);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        cplx<R> v = diag * xs.c[k] - half * acc[rr].c[k];
+        r.c[k] = (k < 6) ? v : R(-1) * v;
+      }
+    }
+    const R s1 = R(e.s1);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) r.c[k] = s1 * r.c[k];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      if (e.v[j] != nullptr) {
+        Spinor<R> vj;
+        load_spinor_as<ST, R>(static_cast<const char*>(e.v[j]) + off, s, V, vj);
+        const R wj = R(e.w[j]);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) r.c[k] = r.c[k] + wj * vj.c[k];
+      }
+    }
+    if (e.z != nullptr) {
+      Spinor<R> zv;
+      load_spinor_as<OT, R>(static_cast<const char*>(e.z) + ooff, s, V, zv);
+      const R wz = R(e.wz);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) r.c[k] = r.c[k] + wz * zv.c[k];
+    }
+    if (e.g5_out) {
+#pragma unroll
+      for (int k = 6; k < 12; ++k) r.c[k] = R(-1) * r.c[k];
+    }
+    if (e.y != nullptr) {
+      Spinor<R> yv;
+      load_spinor_as<OT, R>(static_cast<const char*>(e.y) + ooff, s, V, yv);
+      const R c0 = R(e.c0);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) r.c[k] = r.c[k] + c0 * yv.c[k];
+    }
+    store_spinor_as<OT, R>(out + ooff, s, V, r);
+  }
+}
+
+inline Geo make_geo(const LatticeH& gh) {
+  Geo g;
+  for (int i = 0; i < 4; ++i) g.L[i] = gh.L[i];
+  g.V = (int)gh.V;
+  g.LxLy = gh.L[0] * gh.L[1];
+  g.antiperiodic_t = gh.antiperiodic_t;
+  return g;
+}
+
+inline EpiDev make_epi(const EpiArgs& ea) {
+  EpiDev e;
+  e.wilson = ea.wilson;
+  e.g5_out = ea.g5_out;
+  e.m_w = ea.m_w;
+  e.s1 = ea.s1;
+  e.c0 = ea.c0;
+  e.wz = ea.wz;
+  e.y = ea.y;
+  e.z = ea.z;
+  for (int j = 0; j < 3; ++j) {
+    e.v[j] = ea.v[j];
+    e.w[j] = ea.w[j];
+  }
+  return e;
+}
+
+template <class LT, int LREC, class ST, class OT, int MINB, int RT>
+void launch_k(const LatticeH& gh, const void* links, const void* in, void* out, const EpiArgs& ea, int nrhs, int tpb,
+              cudaStream_t st) {
+  const Geo g = make_geo(gh);
+  const long long rb = (long long)Store<ST>::bytes_per_site * g.V, orb = (long long)Store<OT>::bytes_per_site * g.V;
+  dim3 grid((unsigned)((g.LxLy + tpb - 1) / tpb), (unsigned)(gh.L[2] * gh.L[3]), (unsigned)((nrhs + RT - 1) / RT));
+  k_dslash<LT, LREC, ST, OT, MINB, RT><<<grid, tpb, 0, st>>>(g, links, static_cast<const char*>(in),
+                                                              static_cast<char*>(out), make_epi(ea), rb, orb, nrhs);
+}
+
+// Variant table: (minb, rt) pairs compiled for each storage combination.
+template <class LT, int LREC, class ST, class OT>
+bool launch_variant(const DslashCfg& c, const LatticeH& g, const void* links, const void* in, void* out,
+                    const EpiArgs& e, int nrhs, cudaStream_t st) {
+#define OV_V(MB, RTV)                                                                 \
+  if (c.minb == MB && c.rt == RTV) {                                                  \
+    launch_k<LT, LREC, ST, OT, MB, RTV>(g, links, in, out, e, nrhs, c.tpb, st);       \
+    return true;                                                                      \
+  }
+  OV_V(2, 1) OV_V(3, 1) OV_V(4, 1)
+  if constexpr (!std::is_same<ST, F64>::value) {
+    OV_V(2, 2) OV_V(3, 2) OV_V(1, 4) OV_V(2, 4)
+  }
+#undef OV_V
+  return false;
+}
+
+}  // namespace ov

@@ -43,14 +43,15 @@ void launch_random_block(OpPrec p, void* out, int m, int64_t V, uint64_t seed, c
 
 // --- Gram matrix --------------------------------------------------------------
 // Each CTA stages kGramSites sites of every vector of both blocks in shared
-// memory (as complex in the arithmetic type), then each thread accumulates a
+// memory (as complex in the arithmetic type; B optionally multiplied by
+// gamma5), then each thread accumulates a
 // 4 x 4 tile of (i, j) pairs.  Per-chunk sums in R, running sums in FP64.
 constexpr int kGramSites = 8;
 constexpr int kGramMax = 64;  // max vectors per block (per side)
 
 template <class T>
 __global__ void __launch_bounds__(256) k_gram(const char* __restrict__ A, int ma, const char* __restrict__ B, int mb,
-                                              int64_t V, double2* __restrict__ partial) {
+                                              int64_t V, double2* __restrict__ partial, int g5b) {
   using R = typename Store<T>::R;
   extern __shared__ unsigned char smem_raw[];
   cplx<R>* sa = reinterpret_cast<cplx<R>*>(smem_raw);                 // [ma][kGramSites*12]
@@ -75,6 +76,10 @@ __global__ void __launch_bounds__(256) k_gram(const char* __restrict__ A, int ma
       if (s < V) {
         const char* base = (v < ma) ? A + (int64_t)v * vbytes : B + (int64_t)(v - ma) * vbytes;
         load_spinor<T, R>(base, s, V, x);
+        if (g5b && v >= ma) {
+#pragma unroll
+          for (int k = 6; k < 12; ++k) x.c[k] = R(-1) * x.c[k];
+        }
       } else {
 #pragma unroll
         for (int k = 0; k < 12; ++k) x.c[k] = {R(0), R(0)};
@@ -131,16 +136,16 @@ size_t gram_smem_bytes(OpPrec p) {
 int gram_max_vectors() { return kGramMax; }
 
 cudaError_t launch_gram(OpPrec p, const void* A, int ma, const void* B, int mb, int64_t V, double2* partial,
-                        int nblk, cudaStream_t st) {
+                        int nblk, cudaStream_t st, int g5b) {
   const size_t sm = gram_smem_bytes(p);
   if (p == OP_F64) {
     cudaError_t e = cudaFuncSetAttribute(k_gram<F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_gram<F64><<<nblk, 256, sm, st>>>(static_cast<const char*>(A), ma, static_cast<const char*>(B), mb, V, partial);
+    k_gram<F64><<<nblk, 256, sm, st>>>(static_cast<const char*>(A), ma, static_cast<const char*>(B), mb, V, partial, g5b);
   } else {
     cudaError_t e = cudaFuncSetAttribute(k_gram<F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_gram<F32><<<nblk, 256, sm, st>>>(static_cast<const char*>(A), ma, static_cast<const char*>(B), mb, V, partial);
+    k_gram<F32><<<nblk, 256, sm, st>>>(static_cast<const char*>(A), ma, static_cast<const char*>(B), mb, V, partial, g5b);
   }
   return cudaGetLastError();
 }

@@ -46,15 +46,17 @@ struct EpiArgs {
 
 // Launch shape and link layout of the stencil (chosen per operator by the
 // autotuner): threads per block over an (x, y) plane, a register cap (minb
-// 2 / 3 / 4 = at most 128 / 85 / 64 registers), and for 16-bit links 12 (rows 0, 1; row 2 rebuilt)
+// 1 / 2 / 3 / 4 = none / 128 / 80 / 64 registers), right-hand sides per thread, and for 16-bit links 12 (rows 0, 1; row 2 rebuilt)
 // or 18 stored reals.
 struct DslashCfg {
   int tpb = 128;
   int minb = 2;
   int lrec = 12;
+  int rt = 1;  // right-hand sides per thread (each link loaded once for all of them)
 };
 
-void launch_dslash(OpPrec p, OpPrec out_prec, const DslashCfg& cfg, const LatticeH& g, const void* links,
+// Returns false if the (minb, rt) variant is not compiled for this storage.
+bool launch_dslash(OpPrec p, OpPrec out_prec, const DslashCfg& cfg, const LatticeH& g, const void* links,
                    const void* in, void* out, const EpiArgs& e, int nrhs, cudaStream_t st);
 
 // ---- vector kernels (blas.cu) ---------------------------------------------
@@ -88,9 +90,9 @@ void launch_reduce_partials(const double2* partial, int n, int nblk, double2* ou
 //   psi_perp = scale * (G psi - sum_i c_i phi_i),   d = scale * sum_i sgn_i c_i phi_i
 // (d skipped when null; G = gamma5 if g5).
 // phi, psi and d are in storage pv (FP64 or FP32), psi_perp in pp (the
-// operator's recurrence storage).
+// operator's recurrence storage); c_i is read at c[i * cstride].
 void launch_defl_combine(OpPrec pv, OpPrec pp, const LatticeH& g, const void* evecs, int n_ev,
-                         const double2* c, const double* sgn, const void* psi, int g5, double scale,
+                         const double2* c, int cstride, const double* sgn, const void* psi, int g5, double scale,
                          void* psi_perp, void* d, cudaStream_t st);
 
 // BLAS-1 on internal spinors of storage p: nrhs fields of V sites each,
@@ -115,9 +117,10 @@ void launch_convert(OpPrec pi, OpPrec po, const void* in, void* out, int64_t V, 
 // ---- eigensolver block kernels (eigs.cu) ------------------------------------
 // Block storage: m vectors of V sites back to back, storage OP_F64 or OP_F32.
 void launch_random_block(OpPrec p, void* out, int m, int64_t V, uint64_t seed, cudaStream_t st);
-// partial[(i*mb + j)*nblk + blk] = block blk's share of <A_i, B_j>; ma, mb <= gram_max_vectors().
+// partial[(i*mb + j)*nblk + blk] = block blk's share of <A_i, G B_j>
+// (G = gamma5 if g5b, else 1); ma, mb <= gram_max_vectors().
 cudaError_t launch_gram(OpPrec p, const void* A, int ma, const void* B, int mb, int64_t V, double2* partial,
-                        int nblk, cudaStream_t st);
+                        int nblk, cudaStream_t st, int g5b = 0);
 int gram_max_vectors();
 // out_j = sum_i Y_i Q[i*m_out + j]   (Q complex FP64 on the device; out must not alias Y)
 void launch_rotate(OpPrec p, const void* Y, int m_in, const double2* Q, int m_out, void* out, int64_t V,
