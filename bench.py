@@ -367,6 +367,32 @@ def extras(args, ctx, links_d, a, b, evals, evecs, psi, vol):
         gbs = stencil_bytes_per_apply(prec, ORDER, N_EV, vol) / (2 * ORDER + 1) / (avg * 1e-3) / 1e9
         res["precisions"][prec] = {"applies_per_s": 1e3 / ms, "ms_per_apply": ms, "stencil_avg_us": avg * 1e3,
                                    "stencil_GBps": gbs, "stencil_frac_of_hbm": gbs / hbm}
+    # batched: the 12 spin-colour point sources in one call (config of the
+    # batched workload), per-RHS rate against the single-RHS rate above
+    from paper_1510_06897_gb300 import inputs as _inp
+    src = torch.from_numpy(_inp.point_sources(DIMS)).cuda()
+    outb = torch.empty_like(src)
+    batched = {}
+    for prec in ("fp16", "fp32"):
+        with Ctx(DIMS, links_d, prec) as c:
+            c.sign_config(ORDER, a, b, evals, evecs)
+            ov_sign_apply(c.handle, src, outb, 12)          # tunes the 12-RHS stencil shape
+            torch.cuda.synchronize()
+            ov_reset_stats(c.handle)
+            ov_set_profiling(c.handle, True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ov_sign_apply(c.handle, src, outb, 12)
+            e1.record()
+            torch.cuda.synchronize()
+            ov_set_profiling(c.handle, False)
+            st = ov_get_stats(c.handle)
+        ms = e0.elapsed_time(e1)
+        single = res["precisions"][prec]["ms_per_apply"]
+        batched[prec] = {"rhs_applies_per_s": 12e3 / ms, "ms_per_12rhs_apply": ms,
+                         "speedup_vs_12_single": 12 * single / ms,
+                         "stencil_share": st["dslash_ms"] / ms}
+    res["batched_12_point_sources"] = batched
     # time to solution, D^dagger D x = D^dagger b to 1e-10 (true residual, FP64 operator)
     solves = {}
     precs = [args.prec] + (["fp64"] if args.fp64_solve else [])
@@ -382,8 +408,46 @@ def extras(args, ctx, links_d, a, b, evals, evecs, psi, vol):
             st = ov_get_stats(c.handle)
         solves[prec] = {"seconds": dt, "iterations": it, "outer": st["outer_iterations"], "true_rel_resid": r,
                         "mu": MU}
+    if "fp64" not in solves:
+        fp64_apply = res["precisions"]["fp64"]["ms_per_apply"] * 1e-3
+        it = solves[args.prec]["iterations"]
+        solves["fp64_estimate"] = {
+            "seconds": 2 * it * fp64_apply, "basis": f"{it} CG iterations x 2 FP64 sign applies x "
+                                                     f"{fp64_apply * 1e3:.0f} ms (run with --fp64-solve to measure)"}
     res["solve_1e-10"] = solves
+    res["gradient"] = gradient_timing()
     return res
+
+
+def gradient_timing():
+    """Adjoint of chi^dagger P(K) chi at 16^3 x 32, order 128, complex64 chi, FP32
+    context: time of ov_sign_poly_grad against one forward P(K) chi apply."""
+    import torch
+    from paper_1510_06897_gb300 import inputs
+    from paper_1510_06897_gb300.binding import Ctx, ov_sign_apply, ov_sign_poly_grad
+    dims = (16, 16, 16, 32)
+    links = torch.from_numpy(inputs.gauge_links(dims, seed=1005)).cuda()
+    chi = torch.from_numpy(inputs.gaussian_source(dims, seed=2005).astype(np.complex64)).cuda()
+    grad = torch.empty((4, 32, 16, 16, 16, 3, 3), dtype=torch.complex128, device="cuda")
+    a, b, order = 0.45, 6.5, 128
+    with Ctx(dims, links, "fp32") as c:
+        c.sign_config(order, a, b)
+        out = torch.empty_like(chi)
+        ov_sign_apply(c.handle, chi, out, 1)
+        ov_sign_poly_grad(c.handle, order, a, b, chi, grad)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            ov_sign_apply(c.handle, chi, out, 1)
+        torch.cuda.synchronize()
+        t_fwd = (time.perf_counter() - t0) / 3
+        t0 = time.perf_counter()
+        for _ in range(3):
+            ov_sign_poly_grad(c.handle, order, a, b, chi, grad)
+        torch.cuda.synchronize()
+        t_grad = (time.perf_counter() - t0) / 3
+    return {"lattice": "16x16x16x32", "order": order, "forward_ms": t_fwd * 1e3, "gradient_ms": t_grad * 1e3,
+            "ratio": t_grad / t_fwd}
 
 
 if __name__ == "__main__":

@@ -222,12 +222,29 @@ __device__ __forceinline__ void store_spinor_as(void* p, int s, int V, const Spi
 // ---------------------------------------------------------------------------
 // link load (direction mu, site s)
 
+__device__ __forceinline__ float __fma_any(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double __fma_any(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// conj(a b - c d) as FMA chains
+template <class R>
+__device__ __forceinline__ cplx<R> conj_cross(cplx<R> a, cplx<R> b, cplx<R> c, cplx<R> d) {
+  R re = a.re * b.re;
+  re = __fma_any(-a.im, b.im, re);
+  re = __fma_any(-c.re, d.re, re);
+  re = __fma_any(c.im, d.im, re);
+  R im = c.re * d.im;
+  im = __fma_any(c.im, d.re, im);
+  im = __fma_any(-a.re, b.im, im);
+  im = __fma_any(-a.im, b.re, im);
+  return {re, im};
+}
+
 template <class R>
 __device__ __forceinline__ void reconstruct_row2(SU3<R>& u) {
   // row2 = conj(row0 x row1)
-  u.u[6] = conj(cmul(u.u[1], u.u[5]) - cmul(u.u[2], u.u[4]));
-  u.u[7] = conj(cmul(u.u[2], u.u[3]) - cmul(u.u[0], u.u[5]));
-  u.u[8] = conj(cmul(u.u[0], u.u[4]) - cmul(u.u[1], u.u[3]));
+  u.u[6] = conj_cross(u.u[1], u.u[5], u.u[2], u.u[4]);
+  u.u[7] = conj_cross(u.u[2], u.u[3], u.u[0], u.u[5]);
+  u.u[8] = conj_cross(u.u[0], u.u[4], u.u[1], u.u[3]);
 }
 
 template <class T, class R>

@@ -32,6 +32,10 @@
 
 namespace ov {
 
+// 16-bit spinors are projected in packed arithmetic (see spin.cuh).
+template <class ST>
+constexpr bool kPacked16 = std::is_same<ST, F16>::value || std::is_same<ST, B16>::value;
+
 template <class LT, int LREC, class R>
 __device__ __forceinline__ void load_link_fmt(const void* p, int mu, int s, int V, SU3<R>& u) {
   if constexpr (LREC == 18 && (std::is_same<LT, F16>::value || std::is_same<LT, B16>::value))
@@ -54,10 +58,16 @@ __device__ __forceinline__ void hop_pair(int s, int n_f, int n_b, R sg_f, R sg_b
 #pragma unroll
     for (int r = 0; r < RT; ++r) {
       if (r < nv) {
-        Spinor<R> p;
-        load_spinor_as<ST, R>(in + r * rhs_bytes, n_f, V, p);
         Half<R> h, uh;
-        project<MU, -1>(p, h);
+        if constexpr (kPacked16<ST>) {
+          uint32_t w[12];
+          load_words16(in + r * rhs_bytes, n_f, V, w);
+          project16<MU, -1, ST>(w, h);
+        } else {
+          Spinor<R> p;
+          load_spinor_as<ST, R>(in + r * rhs_bytes, n_f, V, p);
+          project<MU, -1>(p, h);
+        }
         if (MU == 3) scale_half(h, sg_f);
         mul_u(u, h, uh);
         expand_add<MU, -1>(acc[r], uh);
@@ -70,10 +80,16 @@ __device__ __forceinline__ void hop_pair(int s, int n_f, int n_b, R sg_f, R sg_b
 #pragma unroll
     for (int r = 0; r < RT; ++r) {
       if (r < nv) {
-        Spinor<R> p;
-        load_spinor_as<ST, R>(in + r * rhs_bytes, n_b, V, p);
         Half<R> h, uh;
-        project<MU, +1>(p, h);
+        if constexpr (kPacked16<ST>) {
+          uint32_t w[12];
+          load_words16(in + r * rhs_bytes, n_b, V, w);
+          project16<MU, +1, ST>(w, h);
+        } else {
+          Spinor<R> p;
+          load_spinor_as<ST, R>(in + r * rhs_bytes, n_b, V, p);
+          project<MU, +1>(p, h);
+        }
         if (MU == 3) scale_half(h, sg_b);
         mul_udag(u, h, uh);
         expand_add<MU, +1>(acc[r], uh);
