@@ -85,7 +85,7 @@ typedef struct {
   int stencil_tpb;             /* autotuned stencil launch of the context-precision operator: */
   int stencil_minb;            /*   threads per block, register cap (2/3/4 = 128/85/64 regs), */
   int stencil_lrec;            /*   stored reals per link (12: row 2 rebuilt, 18: all) */
-  int reserved;
+  int tc_gemm_launches;        /* deflation projections run on the tensor cores (several RHS, FP32 vectors) */
 } ov_stats;
 
 /* Creates a context for one lattice and gauge field (Eq. 2 links).  Copies and

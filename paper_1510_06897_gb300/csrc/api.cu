@@ -203,9 +203,28 @@ ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kin
   const bool batched = (n_ev > 0 && nrhs > 1 && n_ev <= gram_max_vectors() && nrhs <= gram_max_vectors());
   if (batched) {
     OV_CK(c->d_gram.ensure(sizeof(double2) * (size_t)n_ev * nrhs * kReduceBlocks));
-    OV_CK(launch_gram(I.pv, I.evecs.p, n_ev, in, nrhs, V, c->d_gram.as<double2>(), kReduceBlocks, c->st, g5in));
-    OV_TRY(launched(c));
-    launch_reduce_partials(c->d_gram.as<double2>(), n_ev * nrhs, kReduceBlocks, c->d_c.as<double2>(), c->st);
+    const char* mode = std::getenv("OV_DEFL_GEMM");
+    const bool tc = I.pv == OP_F32 && n_ev <= tc_gram_max_rows() && nrhs <= tc_gram_max_rhs() &&
+                    !(mode && std::strcmp(mode, "cuda") == 0);
+    int nblk = kReduceBlocks;
+    if (tc) {
+      // tensor cores: one CTA per SM, TF32 x 3 split products
+      nblk = std::min(c->num_sms, kReduceBlocks);
+      OV_CK(c->d_err.ensure(sizeof(int)));
+      OV_CK(cudaMemsetAsync(c->d_err.p, 0, sizeof(int), c->st));
+      OV_CK(launch_tc_gram(I.evecs.p, n_ev, in, nrhs, V, g5in, c->d_gram.as<double2>(), nblk, c->d_err.as<int>(),
+                           c->st));
+      OV_TRY(launched(c));
+      c->stats.tc_gemm_launches++;
+      int herr = 0;
+      OV_CK(cudaMemcpyAsync(&herr, c->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+      OV_CK(cudaStreamSynchronize(c->st));
+      if (herr) return fail(c, OV_ERR_CUDA, "tensor-core projection: a bounded wait expired");
+    } else {
+      OV_CK(launch_gram(I.pv, I.evecs.p, n_ev, in, nrhs, V, c->d_gram.as<double2>(), kReduceBlocks, c->st, g5in));
+      OV_TRY(launched(c));
+    }
+    launch_reduce_partials(c->d_gram.as<double2>(), n_ev * nrhs, nblk, c->d_c.as<double2>(), c->st);
     OV_TRY(launched(c));
   }
   for (int r = 0; r < nrhs; ++r) {
@@ -600,6 +619,12 @@ ov_status ov_create(ov_ctx** ctx, const int dims[4], const void* links, ov_prec 
   c->m_w = m_w;
   c->prec = prec;
   c->st = static_cast<cudaStream_t>(cuda_stream);
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (c->num_sms <= 0) c->num_sms = 148;
+  }
   const void* dl = nullptr;
   ov_status s = stage_in(c, c->stage_links, links, (size_t)V * 4 * 9 * 16, &dl);
   if (s == OV_OK) s = init_inst(c, c->hi, OP_F64, dl);
@@ -627,7 +652,7 @@ ov_status ov_destroy(ov_ctx* c) {
   c->hi.release();
   c->lo.release();
   for (cudaEvent_t ev : c->evs) cudaEventDestroy(ev);
-  for (DevBuf* b : {&c->d_sgn, &c->d_c, &c->d_partial, &c->d_scalars, &c->d_gram, &c->stage_in, &c->stage_out, &c->stage_links,
+  for (DevBuf* b : {&c->d_sgn, &c->d_c, &c->d_partial, &c->d_scalars, &c->d_gram, &c->d_err, &c->stage_in, &c->stage_out, &c->stage_links,
                     &c->o_x, &c->o_r, &c->o_rhs, &c->o_q})
     b->release();
   if (c->h_scalars) cudaFreeHost(c->h_scalars);
@@ -840,7 +865,6 @@ ov_status ov_get_stats(const ov_ctx* c, ov_stats* out) {
   out->stencil_tpb = I.cfg.tpb;
   out->stencil_minb = I.cfg.minb;
   out->stencil_lrec = (I.p == OP_F64) ? 18 : I.cfg.lrec;
-  out->reserved = 0;
   return OV_OK;
 }
 

@@ -142,4 +142,13 @@ void launch_force_pairs(OpPrec p, const LatticeH& g, const void* links, const Fo
 // out: complex128 AoS [4][V][3][3] = P_TA(G^dagger)
 void launch_force_finish(OpPrec p, const void* G, int64_t V, void* out, cudaStream_t st);
 
+// ---- tensor-core deflation projection (tc_gram.cu) ----------------------------
+// partial[(i*mb + j)*nblk + blk] as launch_gram, for FP32 vectors, computed
+// with tcgen05 (TF32 x 3 split products); ma <= tc_gram_max_rows(),
+// mb <= tc_gram_max_rhs().  *err is set to 1 if a bounded wait expired.
+cudaError_t launch_tc_gram(const void* A, int ma, const void* B, int mb, int64_t V, int g5b, double2* partial,
+                           int nblk, int* err, cudaStream_t st);
+int tc_gram_max_rows();
+int tc_gram_max_rhs();
+
 }  // namespace ov

@@ -97,3 +97,29 @@ def test_batched_solve_three_rhs():
         rhs = overlap.overlap_dag(prob["links"], b[r], mu, cfg)
         true_r = rhs - overlap.normal_op(prob["links"], x[r], mu, cfg)
         assert np.linalg.norm(true_r) / np.linalg.norm(rhs) <= 2 * tol
+
+
+@pytest.mark.parametrize("dims,n_ev,nrhs", [((8, 8, 8, 8), 40, 12), ((3, 3, 3, 5), 20, 7)])
+def test_tensor_core_projection(monkeypatch, dims, n_ev, nrhs):
+    """The tcgen05 projection (TF32 x 3) against the CUDA-core FP64-sum Gram
+    kernel on the same inputs, through sign(K) and D^dagger (gamma5 on the
+    input), including a K tail that is not a multiple of the 64-float chunk."""
+    links = inputs.gauge_links(dims, seed=8301)
+    src = inputs.gaussian_source(dims, seed=8302, nrhs=nrhs)
+    evecs = _random_orthonormal(dims, n_ev, 8303)
+    evals = np.linspace(-0.5, 0.5, n_ev) + 0.01
+    a, b, order, mu = 0.5, 6.5, 12, 0.1
+    outs = {}
+    for mode in ("tc", "cuda"):
+        monkeypatch.setenv("OV_DEFL_GEMM", mode)
+        with Ctx(dims, dev(links), "fp32") as c:
+            c.sign_config(order, a, b, evals, dev(evecs))
+            s = host(c.sign(dev(src)))
+            d = host(c.overlap(dev(src), mu, dagger=True))
+            outs[mode] = (s, d, c.stats()["tc_gemm_launches"])
+    assert outs["tc"][2] == 2 and outs["cuda"][2] == 0
+    assert rel(outs["tc"][0], outs["cuda"][0]) < 1e-6
+    assert rel(outs["tc"][1], outs["cuda"][1]) < 1e-6
+    cfg = overlap.SignConfig(chebyshev.coefficients(order, a, b), a, b, evals, evecs)
+    want = np.stack([overlap.sign_apply(links, p, cfg) for p in src])
+    assert rel(outs["tc"][0], want) < 2e-5
