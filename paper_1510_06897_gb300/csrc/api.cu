@@ -227,19 +227,25 @@ ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kin
     launch_reduce_partials(c->d_gram.as<double2>(), n_ev * nrhs, nblk, c->d_c.as<double2>(), c->st);
     OV_TRY(launched(c));
   }
-  for (int r = 0; r < nrhs; ++r) {
-    const char* in_r = static_cast<const char*>(in) + r * vb;
-    double2* cr = batched ? c->d_c.as<double2>() + r : c->d_c.as<double2>() + (size_t)r * std::max(1, n_ev);
-    const int cstride = batched ? nrhs : 1;
-    if (n_ev > 0 && !batched) {
-      launch_defl_dot(I.pv, c->g, I.evecs.p, n_ev, in_r, g5in, c->d_partial.as<double2>(), c->st);
-      OV_TRY(launched(c));
-      launch_reduce_partials(c->d_partial.as<double2>(), n_ev, kReduceBlocks, cr, c->st);
+  if (batched && I.pv == OP_F32 && n_ev <= 128) {
+    launch_defl_combine_multi(I.p, c->g, I.evecs.p, n_ev, c->d_c.as<double2>(), nrhs, c->d_sgn.as<double>(), in,
+                              g5in, scale, I.perp.p, I.d.p, c->st);
+    OV_TRY(launched(c));
+  } else {
+    for (int r = 0; r < nrhs; ++r) {
+      const char* in_r = static_cast<const char*>(in) + r * vb;
+      double2* cr = batched ? c->d_c.as<double2>() + r : c->d_c.as<double2>() + (size_t)r * std::max(1, n_ev);
+      const int cstride = batched ? nrhs : 1;
+      if (n_ev > 0 && !batched) {
+        launch_defl_dot(I.pv, c->g, I.evecs.p, n_ev, in_r, g5in, c->d_partial.as<double2>(), c->st);
+        OV_TRY(launched(c));
+        launch_reduce_partials(c->d_partial.as<double2>(), n_ev, kReduceBlocks, cr, c->st);
+        OV_TRY(launched(c));
+      }
+      launch_defl_combine(I.pv, I.p, c->g, I.evecs.p, n_ev, cr, cstride, c->d_sgn.as<double>(), in_r, g5in, scale,
+                          I.perp.c() + r * pb, n_ev > 0 ? I.d.c() + r * vb : nullptr, c->st);
       OV_TRY(launched(c));
     }
-    launch_defl_combine(I.pv, I.p, c->g, I.evecs.p, n_ev, cr, cstride, c->d_sgn.as<double>(), in_r, g5in, scale,
-                        I.perp.c() + r * pb, n_ev > 0 ? I.d.c() + r * vb : nullptr, c->st);
-    OV_TRY(launched(c));
   }
 
   // S4: backward (Clenshaw) recurrence for f_N(Z) psi_perp, Z = alpha K^2 + beta:

@@ -306,6 +306,104 @@ void launch_defl_combine(OpPrec pv, OpPrec pp, const LatticeH& g, const void* ev
   }
 }
 
+// Several right-hand sides at once (FP32 vectors): thread = (site, float4
+// chunk c = complex 2c, 2c+1), RHS tile of kCombineRB in registers, so each
+// eigenvector chunk is read once per tile instead of once per right-hand side.
+// c[i*cstride_i + r] holds c_i for right-hand side r (the batched projection).
+constexpr int kCombineRB = 4;
+
+template <class TP>
+__global__ void __launch_bounds__(256) k_defl_combine_multi(const float4* __restrict__ evecs, int n_ev,
+                                                            const double2* __restrict__ c, int nrhs,
+                                                            const double* __restrict__ sgn,
+                                                            const float4* __restrict__ psi, int V, int g5,
+                                                            float scale, char* __restrict__ psi_perp,
+                                                            float4* __restrict__ d) {
+  __shared__ float2 cs[128 * kCombineRB];
+  __shared__ float ss[128];
+  const int r0 = blockIdx.y * kCombineRB;
+  const int nv = min(kCombineRB, nrhs - r0);
+  for (int idx = threadIdx.x; idx < n_ev * kCombineRB; idx += blockDim.x) {
+    const int i = idx / kCombineRB, r = idx % kCombineRB;
+    const double2 v = (r < nv) ? c[(int64_t)i * nrhs + r0 + r] : make_double2(0.0, 0.0);
+    cs[idx] = make_float2((float)v.x, (float)v.y);
+  }
+  for (int i = threadIdx.x; i < n_ev; i += blockDim.x) ss[i] = (float)sgn[i];
+  __syncthreads();
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const int ch = blockIdx.z;  // float4 chunk 0..5
+  const int64_t off = (int64_t)ch * V + s;
+  const float gs = (g5 && ch >= 3) ? -1.f : 1.f;  // chunks 3..5 hold spins 2, 3
+  float4 x[kCombineRB], corr[kCombineRB];
+#pragma unroll
+  for (int r = 0; r < kCombineRB; ++r) {
+    x[r] = corr[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r < nv) {
+      const float4 v = __ldg(psi + (int64_t)(r0 + r) * 6 * V + off);
+      x[r] = make_float4(gs * v.x, gs * v.y, gs * v.z, gs * v.w);
+    }
+  }
+  for (int i = 0; i < n_ev; ++i) {
+    const float4 f = __ldg(evecs + (int64_t)i * 6 * V + off);
+    const float si = ss[i];
+#pragma unroll
+    for (int r = 0; r < kCombineRB; ++r) {
+      const float2 ci = cs[i * kCombineRB + r];
+      const float t0r = ci.x * f.x - ci.y * f.y, t0i = ci.x * f.y + ci.y * f.x;
+      const float t1r = ci.x * f.z - ci.y * f.w, t1i = ci.x * f.w + ci.y * f.z;
+      x[r].x -= t0r;
+      x[r].y -= t0i;
+      x[r].z -= t1r;
+      x[r].w -= t1i;
+      corr[r].x += si * t0r;
+      corr[r].y += si * t0i;
+      corr[r].z += si * t1r;
+      corr[r].w += si * t1i;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kCombineRB; ++r) {
+    if (r >= nv) break;
+    const float4 xo = make_float4(scale * x[r].x, scale * x[r].y, scale * x[r].z, scale * x[r].w);
+    d[(int64_t)(r0 + r) * 6 * V + off] =
+        make_float4(scale * corr[r].x, scale * corr[r].y, scale * corr[r].z, scale * corr[r].w);
+    if constexpr (std::is_same<TP, F32>::value) {
+      reinterpret_cast<float4*>(psi_perp)[(int64_t)(r0 + r) * 6 * V + off] = xo;
+    } else {
+      // 16-bit chunk ch/2 holds complex 4*(ch/2) .. +3; this thread's two are its half ch%2
+      uint2 w;
+      w.x = pack2<TP>(xo.x, xo.y);
+      w.y = pack2<TP>(xo.z, xo.w);
+      uint2* q = reinterpret_cast<uint2*>(psi_perp + (int64_t)(r0 + r) * 48 * V);
+      q[((int64_t)(ch >> 1) * V + s) * 2 + (ch & 1)] = w;
+    }
+  }
+}
+
+void launch_defl_combine_multi(OpPrec pp, const LatticeH& g, const void* evecs, int n_ev, const double2* c, int nrhs,
+                               const double* sgn, const void* psi, int g5, double scale, void* psi_perp, void* d,
+                               cudaStream_t st) {
+  dim3 grid(grid_for(g.V), (nrhs + kCombineRB - 1) / kCombineRB, 6);
+  const float4* e = static_cast<const float4*>(evecs);
+  const float4* x = static_cast<const float4*>(psi);
+  char* pp_ = static_cast<char*>(psi_perp);
+  float4* dd = static_cast<float4*>(d);
+  switch (pp) {
+    case OP_F32:
+      k_defl_combine_multi<F32><<<grid, kThreads, 0, st>>>(e, n_ev, c, nrhs, sgn, x, (int)g.V, g5, (float)scale, pp_, dd);
+      break;
+    case OP_F16:
+      k_defl_combine_multi<F16><<<grid, kThreads, 0, st>>>(e, n_ev, c, nrhs, sgn, x, (int)g.V, g5, (float)scale, pp_, dd);
+      break;
+    case OP_B16:
+      k_defl_combine_multi<B16><<<grid, kThreads, 0, st>>>(e, n_ev, c, nrhs, sgn, x, (int)g.V, g5, (float)scale, pp_, dd);
+      break;
+    default:
+      break;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // BLAS-1 on same-storage vectors, treated as flat arrays of complex numbers
 // (layout-agnostic: all operands share the layout).  A "unit" is one storage

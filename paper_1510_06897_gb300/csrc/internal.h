@@ -95,6 +95,12 @@ void launch_defl_combine(OpPrec pv, OpPrec pp, const LatticeH& g, const void* ev
                          const double2* c, int cstride, const double* sgn, const void* psi, int g5, double scale,
                          void* psi_perp, void* d, cudaStream_t st);
 
+// Several right-hand sides with FP32 vectors (n_ev <= 128): c[i*nrhs + r] from
+// the batched projection; psi_perp in pp (FP32 / FP16 / BF16), d in FP32.
+void launch_defl_combine_multi(OpPrec pp, const LatticeH& g, const void* evecs, int n_ev, const double2* c, int nrhs,
+                               const double* sgn, const void* psi, int g5, double scale, void* psi_perp, void* d,
+                               cudaStream_t st);
+
 // BLAS-1 on internal spinors of storage p: nrhs fields of V sites each,
 // stored back to back.  Reductions leave one double2 per block in partial[]
 // (complex dot: re/im; norm: .x), to be summed by launch_reduce_partials.

@@ -14,8 +14,9 @@
 // and restarts it, and at the end writes one FP64 partial per (i, j), which
 // the fixed-order reduction of blas.cu sums.
 //
-// Pipeline per CTA (256 threads): all threads load a 64-float chunk of every
-// row, split it and store it into one of two shared-memory stages in the
+// Pipeline per CTA (512 threads): raw 64-float chunks of every row are copied
+// into a ring of up to four shared-memory buffers with cp.async (several
+// chunks in flight), then split and stored into one of two MMA stages in the
 // canonical no-swizzle K-major layout (8-row x 16-byte core matrices); one
 // thread issues the 24 MMAs of the chunk and commits them to the stage's
 // mbarrier, so the next chunk is loaded while the tensor core works.  Every
@@ -32,14 +33,23 @@ namespace {
 constexpr int kTcM = 128;      // MMA M: rows of A (eigenvectors, zero padded)
 constexpr int kTcN = 32;       // MMA N: 2 x right-hand sides (zero padded)
 constexpr int kTcK = 64;       // floats per chunk and stage
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;
+constexpr int kRawPitch = kTcK * 4 + 16;  // bytes per raw row (padded: conflict-free 16-byte reads)
+constexpr int kRawStagesMax = 4;          // chunks in flight (cp.async ring of raw FP32 rows)
 constexpr int kFlush = 64;     // chunks per tensor-memory accumulation window
 constexpr int kTmemCols = 32;
 
 constexpr uint32_t kTileA = kTcM * kTcK * 4;  // bytes of one A part (hi or lo)
 constexpr uint32_t kTileB = kTcN * kTcK * 4;
 constexpr uint32_t kStage = 2 * kTileA + 2 * kTileB;  // A_hi, A_lo, B_hi, B_lo
-constexpr uint32_t kSmemBytes = 2 * kStage + 1024;     // two stages + control block
+constexpr uint32_t kCtrl = 1024;                         // mbarriers, tensor-memory address
+// dynamic shared memory: two MMA stages, control block, raw ring
+inline uint32_t raw_stages(int rows) {
+  const uint32_t avail = 227u * 1024u - 2 * kStage - kCtrl;
+  const uint32_t per = (uint32_t)rows * kRawPitch;
+  const uint32_t n = avail / per;
+  return n < 1 ? 1 : (n > (uint32_t)kRawStagesMax ? (uint32_t)kRawStagesMax : n);
+}
 
 // byte offset of element (row r, k) inside one part: core matrices of
 // 8 rows x 16 bytes, 16 of them along K (64 floats) per 8-row group.
@@ -124,24 +134,32 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
   lo = x - hi;
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gram(const float* __restrict__ A, int ma, const float* __restrict__ B, int mb, long long K, int g5b,
-              double2* __restrict__ partial, int* __restrict__ err) {
+              double2* __restrict__ partial, int* __restrict__ err, int nraw) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* stage_base = smem;
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + 2 * kStage);  // [0], [1]: stages
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + 2 * kStage + 64);
-  int* timed_out_sm = reinterpret_cast<int*>(smem + 2 * kStage + 128);
+  unsigned char* raw_base = smem + 2 * kStage + kCtrl;
+  const int rows = ma + mb;
+  const uint32_t raw_stage_bytes = (uint32_t)rows * kRawPitch;
   const int tid = threadIdx.x, warp = tid >> 5;
   const long long half_k = K / 2;  // gamma5 flips the second half of each vector (spins 2, 3)
 
-  // zero both stages once: rows >= ma / >= 2 mb and the K tail stay zero
+  // zero both MMA stages once: rows >= ma / >= 2 mb stay zero
   for (uint32_t i = tid; i < 2 * kStage / 16; i += kTcThreads)
     reinterpret_cast<uint4*>(stage_base)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
     mbar_init(smem_u32(&bars[0]), 1);
     mbar_init(smem_u32(&bars[1]), 1);
-    *timed_out_sm = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -156,6 +174,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t tmem = *tmem_holder;
 
   const long long nchunks = (K + kTcK - 1) / kTcK;
+  // raw copy of chunk `chk` into ring slot `slot`: 16 bytes per thread-iteration,
+  // zero-filled past K and for chunks past the end
+  auto issue = [&](long long chk, int slot) {
+    const uint32_t dst0 = smem_u32(raw_base + (uint32_t)slot * raw_stage_bytes);
+    const long long k0 = chk * kTcK;
+    for (int idx = tid; idx < rows * (kTcK / 4); idx += kTcThreads) {
+      const int row = idx / (kTcK / 4), q = idx % (kTcK / 4);
+      const long long k = k0 + 4 * q;
+      const bool ok = chk < nchunks && k < K;
+      const float* src = (row < ma) ? A + (long long)row * K : B + (long long)(row - ma) * K;
+      cp_async16(dst0 + (uint32_t)row * kRawPitch + 16u * q, ok ? src + k : A, ok ? 16u : 0u);
+    }
+    cp_async_commit();
+  };
+
   double acc[32];
 #pragma unroll
   for (int i = 0; i < 32; ++i) acc[i] = 0.0;
@@ -184,52 +217,47 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_after();
   };
 
+  // prologue: nraw - 1 chunks in flight
+  for (int p = 0; p < nraw - 1; ++p) issue(blockIdx.x + (long long)p * gridDim.x, p);
+
   for (long long ch = blockIdx.x; ch < nchunks && !failed; ch += gridDim.x) {
     const int stage = it & 1;
     const uint32_t use = (uint32_t)(it >> 1);
     unsigned char* st = stage_base + stage * kStage;
-    if (use >= 1) {  // the MMAs that last read this stage must be complete
-      const bool ok = mbar_wait(smem_u32(&bars[stage]), (use - 1) & 1);
-      if (__syncthreads_or(!ok)) {
-        failed = true;
-        break;
-      }
+    const int slot = it % nraw;
+    issue(ch + (long long)(nraw - 1) * gridDim.x, (it + nraw - 1) % nraw);
+    // this thread's copies of chunk ch have landed (newer groups may still fly)
+    if (nraw == 4) cp_async_wait<3>();
+    else if (nraw == 3) cp_async_wait<2>();
+    else if (nraw == 2) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    bool ok = true;
+    if (use >= 1) ok = mbar_wait(smem_u32(&bars[stage]), (use - 1) & 1);  // stage free again
+    if (__syncthreads_or(!ok)) {  // also makes every thread's raw copies visible
+      failed = true;
+      break;
     }
+    // split raw rows into TF32 hi / lo tiles; consecutive threads take
+    // consecutive rows (conflict-free 16-byte reads and writes)
+    const unsigned char* raw = raw_base + (uint32_t)slot * raw_stage_bytes;
     const long long k0 = ch * kTcK;
-    // A rows.  Consecutive threads take consecutive rows (conflict-free
-    // 16-byte shared stores); each thread moves one 32-byte sector (8 floats).
-    for (int idx = tid; idx < ma * (kTcK / 8); idx += kTcThreads) {
-      const int r = idx % ma, q8 = idx / ma;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int kq = 8 * q8 + 4 * h;
-        const long long k = k0 + kq;
-        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (k < K) x = __ldg(reinterpret_cast<const float4*>(A + (long long)r * K + k));
-        float4 hi, lo;
+    for (int idx = tid; idx < rows * (kTcK / 4); idx += kTcThreads) {
+      const int row = idx % rows, q = idx / rows;
+      float4 x = *reinterpret_cast<const float4*>(raw + (uint32_t)row * kRawPitch + 16u * q);
+      float4 hi, lo;
+      if (row < ma) {
         split_tf32(x.x, hi.x, lo.x);
         split_tf32(x.y, hi.y, lo.y);
         split_tf32(x.z, hi.z, lo.z);
         split_tf32(x.w, hi.w, lo.w);
-        const uint32_t off = tile_off(r, kq);
+        const uint32_t off = tile_off(row, 4 * q);
         *reinterpret_cast<float4*>(st + off) = hi;
         *reinterpret_cast<float4*>(st + kTileA + off) = lo;
-      }
-    }
-    // B rows: b_j in row j, b~_j = (b_im, -b_re) pairs in row mb + j
-    for (int idx = tid; idx < mb * (kTcK / 8); idx += kTcThreads) {
-      const int j = idx % mb, q8 = idx / mb;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int kq = 8 * q8 + 4 * h;
-        const long long k = k0 + kq;
-        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (k < K) {
-          x = __ldg(reinterpret_cast<const float4*>(B + (long long)j * K + k));
-          if (g5b && k >= half_k) x = make_float4(-x.x, -x.y, -x.z, -x.w);
-        }
+      } else {
+        const int j = row - ma;
+        if (g5b && k0 + 4 * q >= half_k) x = make_float4(-x.x, -x.y, -x.z, -x.w);
         const float4 xt = make_float4(x.y, -x.x, x.w, -x.z);
-        float4 hi, lo, thi, tlo;
+        float4 thi, tlo;
         split_tf32(x.x, hi.x, lo.x);
         split_tf32(x.y, hi.y, lo.y);
         split_tf32(x.z, hi.z, lo.z);
@@ -238,7 +266,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         split_tf32(xt.y, thi.y, tlo.y);
         split_tf32(xt.z, thi.z, tlo.z);
         split_tf32(xt.w, thi.w, tlo.w);
-        const uint32_t off = tile_off(j, kq), offt = tile_off(mb + j, kq);
+        const uint32_t off = tile_off(j, 4 * q), offt = tile_off(mb + j, 4 * q);
         *reinterpret_cast<float4*>(st + 2 * kTileA + off) = hi;
         *reinterpret_cast<float4*>(st + 2 * kTileA + kTileB + off) = lo;
         *reinterpret_cast<float4*>(st + 2 * kTileA + offt) = thi;
@@ -250,14 +278,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncthreads();
     tc_fence_after();
     if (tid == 0) {
-      const uint32_t a_hi = smem_u32(st), a_lo = a_hi + kTileA, b_hi = a_hi + 2 * kTileA, b_lo = b_hi + kTileB;
+      // the descriptor's address field is addr >> 4 in its low bits (all of
+      // this CTA's shared memory stays below 2^18 bytes), so sub-tiles and
+      // K steps are plain offsets of one base descriptor
+      const uint64_t d_ahi = smem_desc(smem_u32(st));
+      const uint64_t d_alo = d_ahi + (kTileA >> 4), d_bhi = d_ahi + ((2 * kTileA) >> 4);
+      const uint64_t d_blo = d_bhi + (kTileB >> 4);
 #pragma unroll
       for (int kk = 0; kk < kTcK / 8; ++kk) {
-        const uint32_t koff = (uint32_t)kk * 256;  // 8 floats = two core matrices along K
+        const uint64_t o = (uint64_t)kk * (256 >> 4);  // 8 floats = two core matrices along K
         const uint32_t acc_in = (in_window > 0 || kk > 0) ? 1u : 0u;
-        tc_mma(tmem, smem_desc(a_hi + koff), smem_desc(b_hi + koff), acc_in);
-        tc_mma(tmem, smem_desc(a_hi + koff), smem_desc(b_lo + koff), 1u);
-        tc_mma(tmem, smem_desc(a_lo + koff), smem_desc(b_hi + koff), 1u);
+        tc_mma(tmem, d_ahi + o, d_bhi + o, acc_in);
+        tc_mma(tmem, d_ahi + o, d_blo + o, 1u);
+        tc_mma(tmem, d_alo + o, d_bhi + o, 1u);
       }
       tc_commit(smem_u32(&bars[stage]));
     }
@@ -267,6 +300,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     ++in_window;
     if (in_window == kFlush) flush();
   }
+  cp_async_wait<0>();  // no copy may still target shared memory when the CTA exits
   if (!failed) flush();
   if (failed) {
     if (tid == 0) atomicExch(err, 1);
@@ -295,10 +329,12 @@ int tc_gram_max_rhs() { return kTcN / 2; }
 cudaError_t launch_tc_gram(const void* A, int ma, const void* B, int mb, int64_t V, int g5b, double2* partial,
                            int nblk, int* err, cudaStream_t st) {
   if (ma < 1 || ma > kTcM || mb < 1 || 2 * mb > kTcN) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  const uint32_t nraw = raw_stages(ma + mb);
+  const uint32_t smem = 2 * kStage + kCtrl + nraw * (uint32_t)(ma + mb) * kRawPitch;
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_tc_gram<<<nblk, kTcThreads, kSmemBytes, st>>>(static_cast<const float*>(A), ma, static_cast<const float*>(B),
-                                                  mb, 24LL * V, g5b, partial, err);
+  k_tc_gram<<<nblk, kTcThreads, smem, st>>>(static_cast<const float*>(A), ma, static_cast<const float*>(B), mb,
+                                            24LL * V, g5b, partial, err, (int)nraw);
   return cudaGetLastError();
 }
 
