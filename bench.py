@@ -69,10 +69,13 @@ def measured_peaks():
 def ncu_traffic(prec):
     """DRAM bytes per site per stencil launch from the committed ncu summary,
     if it was taken on the current stencil source (else None)."""
-    src = os.path.join(ROOT, "paper_1510_06897_gb300", "csrc", "dslash_kernel.cuh")
+    csrc = os.path.join(ROOT, "paper_1510_06897_gb300", "csrc")
     path = os.path.join(ROOT, "profiles", "dslash_24x24x24x48.md")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256()
+        for name in ("dslash_kernel.cuh", "spin.cuh", "common.cuh"):  # everything the stencil is built from
+            h.update(open(os.path.join(csrc, name), "rb").read())
+        sha = h.hexdigest()[:16]
         text = open(path).read()
     except OSError:
         return None
