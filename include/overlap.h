@@ -97,7 +97,10 @@ typedef struct {
  * OV_ERR_NOMEM, OV_ERR_CUDA.
  * The stencil's launch shape and (16-bit) link layout are autotuned here by
  * timing a few launches of each variant on this lattice; the environment
- * variable OV_STENCIL="tpb,minb,lrec" pins one variant instead (see ov_stats). */
+ * variable OV_STENCIL="tpb,minb,lrec" pins one variant instead (see ov_stats).
+ * For 16-bit precisions the links are marked persisting in L2 for the stencil
+ * launches (a per-process limit set here and released by ov_destroy;
+ * OV_L2PIN=0 disables it). */
 ov_status ov_create(ov_ctx** ctx, const int dims[4], const void* links, ov_prec prec, double m_w,
                     int antiperiodic_t, void* cuda_stream);
 

@@ -580,7 +580,23 @@ ov_status init_inst(ov_ctx* c, Inst& I, OpPrec p, const void* links_dev) {
   OV_CK(I.links.ensure((size_t)link_bytes_per_site_dir(p, 12) * 4 * c->g.V));
   launch_pack_links(p, 12, c->g, links_dev, I.links.p, c->st);
   OV_TRY(launched(c));
-  return autotune(c, I, links_dev);
+  OV_TRY(autotune(c, I, links_dev));
+  // 16-bit links fit in L2: mark them persisting for the stencil launches
+  // (a per-process limit, released in ov_destroy).  OV_L2PIN=0 disables.
+  const char* pin = std::getenv("OV_L2PIN");
+  if ((p == OP_F16 || p == OP_B16) && !(pin && std::atoi(pin) == 0)) {
+    const size_t bytes = (size_t)link_bytes_per_site_dir(p, I.cfg.lrec) * 4 * c->g.V;
+    int dev = 0, max_persist = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev) == cudaSuccess &&
+        (size_t)max_persist >= bytes && bytes >= (size_t(1) << 20)) {
+      OV_CK(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, bytes));
+      l2_window().base = I.links.p;
+      l2_window().bytes = bytes;
+      c->l2_pinned = true;
+    }
+  }
+  return OV_OK;
 }
 
 }  // namespace ov
@@ -655,6 +671,11 @@ ov_status ov_create(ov_ctx** ctx, const int dims[4], const void* links, ov_prec 
 ov_status ov_destroy(ov_ctx* c) {
   if (!c) return OV_OK;
   cudaStreamSynchronize(c->st);
+  if (c->l2_pinned) {
+    if (l2_window().base == c->lo.links.p) l2_window() = L2Window{};
+    cudaCtxResetPersistingL2Cache();
+    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, 0);
+  }
   c->hi.release();
   c->lo.release();
   for (cudaEvent_t ev : c->evs) cudaEventDestroy(ev);

@@ -72,6 +72,7 @@ struct ov_ctx {
   std::vector<double> evals, sgn;
   DevBuf d_sgn, d_c, d_partial, d_scalars, d_gram, d_err;
   int num_sms = 0;
+  bool l2_pinned = false;  // this context set the persisting-L2 window over its links
   DevBuf stage_in, stage_out, stage_links;
   DevBuf o_x, o_r, o_rhs, o_q;  // FP64 outer-solver vectors
   double* h_scalars = nullptr;  // pinned

@@ -1,8 +1,13 @@
 // Stencil dispatch: picks the per-precision launcher compiled in
 // dslash_f64.cu / dslash_f32.cu / dslash_f16.cu / dslash_b16.cu.
-#include "internal.h"
+#include "dslash_kernel.cuh"
 
 namespace ov {
+
+L2Window& l2_window() {
+  static L2Window w;
+  return w;
+}
 
 bool launch_dslash_f64(const DslashCfg&, OpPrec, const LatticeH&, const void*, const void*, void*, const EpiArgs&, int,
                        cudaStream_t);

@@ -245,6 +245,25 @@ void launch_k(const LatticeH& gh, const void* links, const void* in, void* out, 
   const Geo g = make_geo(gh);
   const long long rb = (long long)Store<ST>::bytes_per_site * g.V, orb = (long long)Store<OT>::bytes_per_site * g.V;
   dim3 grid((unsigned)((g.LxLy + tpb - 1) / tpb), (unsigned)(gh.L[2] * gh.L[3]), (unsigned)((nrhs + RT - 1) / RT));
+  const L2Window& w = l2_window();
+  if (w.base != nullptr && w.base == links) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(tpb);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[0].val.accessPolicyWindow.base_ptr = const_cast<void*>(w.base);
+    attr[0].val.accessPolicyWindow.num_bytes = w.bytes;
+    attr[0].val.accessPolicyWindow.hitRatio = 1.0f;
+    attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_dslash<LT, LREC, ST, OT, MINB, RT>, g, links, static_cast<const char*>(in),
+                       static_cast<char*>(out), make_epi(ea), rb, orb, nrhs);
+    return;
+  }
   k_dslash<LT, LREC, ST, OT, MINB, RT><<<grid, tpb, 0, st>>>(g, links, static_cast<const char*>(in),
                                                               static_cast<char*>(out), make_epi(ea), rb, orb, nrhs);
 }

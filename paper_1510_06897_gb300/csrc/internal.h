@@ -55,6 +55,14 @@ struct DslashCfg {
   int rt = 1;  // right-hand sides per thread (each link loaded once for all of them)
 };
 
+// Optional L2 access-policy window (persisting) applied to stencil launches
+// whose links pointer is `base`.
+struct L2Window {
+  const void* base = nullptr;
+  size_t bytes = 0;
+};
+L2Window& l2_window();
+
 // Returns false if the (minb, rt) variant is not compiled for this storage.
 bool launch_dslash(OpPrec p, OpPrec out_prec, const DslashCfg& cfg, const LatticeH& g, const void* links,
                    const void* in, void* out, const EpiArgs& e, int nrhs, cudaStream_t st);
