@@ -29,8 +29,8 @@ def _gpu():
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
-@pytest.mark.parametrize("dims,antiperiodic", [((4, 4, 4, 4), False), ((6, 4, 2, 8), True), ((8, 8, 8, 8), False),
-                                              ((16, 16, 16, 32), True)])
+@pytest.mark.parametrize("dims,antiperiodic", [((2, 2, 2, 2), False), ((4, 4, 4, 4), False), ((6, 4, 2, 8), True),
+                                              ((8, 8, 8, 8), False), ((16, 16, 16, 32), True)])
 def test_wilson_and_kernel(prec, dims, antiperiodic):
     links = inputs.gauge_links(dims, seed=4001)
     psi = inputs.gaussian_source(dims, seed=4002, nrhs=2)
@@ -135,6 +135,19 @@ def test_free_field_sign_full_size():
             cx.sign_config(order, a, b)
             got = host(cx.sign(dev(psi)))
         assert rel(got, want) < tol, prec
+
+
+def test_empty_and_bad_inputs():
+    dims = (4, 4, 4, 4)
+    links = inputs.gauge_links(dims, seed=4601)
+    psi = dev(inputs.gaussian_source(dims, seed=4602))
+    from paper_1510_06897_gb300.binding import ov_wilson
+    with Ctx(dims, dev(links), "fp32") as c:
+        with pytest.raises(OverlapError) as e:
+            ov_wilson(c.handle, psi, torch.empty_like(psi), 0)   # no right-hand side
+        assert e.value.status == 1
+        with pytest.raises(OverlapError):
+            c.solve(psi, mu=float("nan"))
 
 
 def test_errors_and_state():
