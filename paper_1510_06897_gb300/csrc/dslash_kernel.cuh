@@ -47,10 +47,10 @@ __device__ __forceinline__ void load_link_fmt(const void* p, int mu, int s, int 
 // Both hops of direction MU for site s and the RT right-hand sides of this
 // thread (fields rhs_bytes apart, the last nv of them valid): the link of
 // each hop is loaded (and rebuilt) once and applied to every right-hand side.
-// n_f / n_b are the neighbour indices, sg_f / sg_b the boundary signs (-1
+// n_f / n_b are the neighbour indices; neg_f / neg_b flip the sign (-1
 // across an antiperiodic t boundary).
 template <int MU, class LT, int LREC, class ST, int RT, class R>
-__device__ __forceinline__ void hop_pair(int s, int n_f, int n_b, R sg_f, R sg_b, int V, const void* links,
+__device__ __forceinline__ void hop_pair(int s, int n_f, int n_b, bool neg_f, bool neg_b, int V, const void* links,
                                          const char* in, long long rhs_bytes, int nv, Spinor<R> (&acc)[RT]) {
   {  // forward: (1 - gamma_mu) U_mu(s) x(s + mu^)
     SU3<R> u;
@@ -68,7 +68,7 @@ __device__ __forceinline__ void hop_pair(int s, int n_f, int n_b, R sg_f, R sg_b
           load_spinor_as<ST, R>(in + r * rhs_bytes, n_f, V, p);
           project<MU, -1>(p, h);
         }
-        if (MU == 3) scale_half(h, sg_f);
+        if (MU == 3 && neg_f) scale_half(h, R(-1));  // block-uniform: a block is one (z, t) slice
         mul_u(u, h, uh);
         expand_add<MU, -1>(acc[r], uh);
       }
@@ -90,7 +90,7 @@ __device__ __forceinline__ void hop_pair(int s, int n_f, int n_b, R sg_f, R sg_b
           load_spinor_as<ST, R>(in + r * rhs_bytes, n_b, V, p);
           project<MU, +1>(p, h);
         }
-        if (MU == 3) scale_half(h, sg_b);
+        if (MU == 3 && neg_b) scale_half(h, R(-1));
         mul_udag(u, h, uh);
         expand_add<MU, +1>(acc[r], uh);
       }
@@ -145,18 +145,18 @@ __global__ void __launch_bounds__(256, MINB) k_dslash(Geo g, const void* __restr
   const int zm = (z == 0) ? s + (Lz - 1) * sz : s - sz;
   const int tp = (t == Lt - 1) ? s - (Lt - 1) * st : s + st;
   const int tm = (t == 0) ? s + (Lt - 1) * st : s - st;
-  const R sg_tf = (g.antiperiodic_t && t == Lt - 1) ? R(-1) : R(1);
-  const R sg_tb = (g.antiperiodic_t && t == 0) ? R(-1) : R(1);
+  const bool neg_tf = g.antiperiodic_t && t == Lt - 1;  // antiperiodic wrap of the t hops
+  const bool neg_tb = g.antiperiodic_t && t == 0;
 
   Spinor<R> acc[RT];
 #pragma unroll
   for (int r = 0; r < RT; ++r)
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[r].c[k] = {R(0), R(0)};
-  hop_pair<0, LT, LREC, ST, RT>(s, xp, xm, R(1), R(1), V, links, xin, rhs_bytes, nv, acc);
-  hop_pair<1, LT, LREC, ST, RT>(s, yp, ym, R(1), R(1), V, links, xin, rhs_bytes, nv, acc);
-  hop_pair<2, LT, LREC, ST, RT>(s, zp, zm, R(1), R(1), V, links, xin, rhs_bytes, nv, acc);
-  hop_pair<3, LT, LREC, ST, RT>(s, tp, tm, sg_tf, sg_tb, V, links, xin, rhs_bytes, nv, acc);
+  hop_pair<0, LT, LREC, ST, RT, R>(s, xp, xm, false, false, V, links, xin, rhs_bytes, nv, acc);
+  hop_pair<1, LT, LREC, ST, RT, R>(s, yp, ym, false, false, V, links, xin, rhs_bytes, nv, acc);
+  hop_pair<2, LT, LREC, ST, RT, R>(s, zp, zm, false, false, V, links, xin, rhs_bytes, nv, acc);
+  hop_pair<3, LT, LREC, ST, RT, R>(s, tp, tm, neg_tf, neg_tb, V, links, xin, rhs_bytes, nv, acc);
 
 #pragma unroll
   for (int rr = 0; rr < RT; ++rr) {
