@@ -86,6 +86,8 @@ typedef struct {
   int stencil_minb;            /*   threads per block, register cap (2/3/4 = 128/85/64 regs), */
   int stencil_lrec;            /*   stored reals per link (12: row 2 rebuilt, 18: all) */
   int tc_gemm_launches;        /* deflation projections run on the tensor cores (several RHS, FP32 vectors) */
+  int stencil_slab;            /* > 0: the tuned stencil is the slab kernel on this many persistent CTAs
+                                  (stencil_tpb = Lx*Ly + 32 threads each); 0: the gather kernel */
 } ov_stats;
 
 /* Creates a context for one lattice and gauge field (Eq. 2 links).  Copies and
@@ -97,7 +99,8 @@ typedef struct {
  * OV_ERR_NOMEM, OV_ERR_CUDA.
  * The stencil's launch shape and (16-bit) link layout are autotuned here by
  * timing a few launches of each variant on this lattice; the environment
- * variable OV_STENCIL="tpb,minb,lrec" pins one variant instead (see ov_stats).
+ * variable OV_STENCIL="tpb,minb,lrec" pins one gather variant, OV_STENCIL="slab"
+ * the slab kernel where it applies (see ov_stats).
  * For 16-bit precisions the links are marked persisting in L2 for the stencil
  * launches (a per-process limit set here and released by ov_destroy;
  * OV_L2PIN=0 disables it). */

@@ -44,7 +44,8 @@ class ov_stats(ctypes.Structure):
                 ("stencil_tpb", ctypes.c_int),
                 ("stencil_minb", ctypes.c_int),
                 ("stencil_lrec", ctypes.c_int),
-                ("tc_gemm_launches", ctypes.c_int)]
+                ("tc_gemm_launches", ctypes.c_int),
+                ("stencil_slab", ctypes.c_int)]
 
 
 _LIB = None

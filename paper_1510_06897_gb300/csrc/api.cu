@@ -72,11 +72,21 @@ ov_status stage_out(ov_ctx* c, void* p, size_t bytes, void** out, bool* staged) 
   return OV_OK;
 }
 
+// After a stream sync: a slab stencil launch whose bulk copies did not land
+// in time left its flag set.
+ov_status stencil_status(ov_ctx* c) {
+  if (c->h_stencil_err && *static_cast<volatile int*>(c->h_stencil_err)) {
+    *c->h_stencil_err = 0;
+    return fail(c, OV_ERR_CUDA, "stencil: a shared-memory bulk copy did not complete in time");
+  }
+  return OV_OK;
+}
+
 ov_status finish_out(ov_ctx* c, void* host, size_t bytes, bool staged) {
   if (staged) OV_CK(cudaMemcpyAsync(host, c->stage_out.p, bytes, cudaMemcpyDeviceToHost, c->st));
   OV_CK(cudaStreamSynchronize(c->st));
   prof_collect(c);
-  return OV_OK;
+  return stencil_status(c);
 }
 
 void prof_collect(ov_ctx* c) {
@@ -141,6 +151,7 @@ ov_status read_reduced(ov_ctx* c, const double2* partial, int n, double2* out) {
   OV_CK(cudaMemcpyAsync(c->h_scalars, c->d_scalars.p, sizeof(double2) * n, cudaMemcpyDeviceToHost, c->st));
   OV_CK(cudaStreamSynchronize(c->st));
   prof_collect(c);
+  OV_TRY(stencil_status(c));
   std::memcpy(out, c->h_scalars, sizeof(double2) * n);
   return OV_OK;
 }
@@ -445,11 +456,18 @@ ov_status time_variant(ov_ctx* c, Inst& I, const DslashCfg& cfg, const void* lin
 const int kVariants[][2] = {{2, 1}, {3, 1}, {4, 1}, {2, 2}, {3, 2}, {1, 4}, {2, 4}};
 
 // The environment variable OV_STENCIL="tpb,minb,lrec[,rt]" (e.g. "192,3,12")
-// skips the timing and pins one variant (used for reproducible profiles).
+// skips the timing and pins one variant (used for reproducible profiles);
+// OV_STENCIL="slab" pins the slab kernel where it applies (16-bit storage,
+// Lx Ly a multiple of 32 up to 640), the default gather variant elsewhere.
 bool pinned_cfg(DslashCfg* cfg, bool* bad) {
   *bad = false;
   const char* env = std::getenv("OV_STENCIL");
   if (!env) return false;
+  if (std::strcmp(env, "slab") == 0) {
+    *cfg = DslashCfg{};
+    cfg->slab = 1;  // resolved by the caller
+    return true;
+  }
   int tpb = 0, minb = 0, lrec = 0, rt = 1;
   const int n = std::sscanf(env, "%d,%d,%d,%d", &tpb, &minb, &lrec, &rt);
   bool ok = n >= 3 && tpb >= 32 && tpb <= 256 && tpb % 32 == 0 && (lrec == 12 || lrec == 18);
@@ -460,6 +478,21 @@ bool pinned_cfg(DslashCfg* cfg, bool* bad) {
     return false;
   }
   *cfg = DslashCfg{tpb, minb, lrec, rt};
+  return true;
+}
+
+// The slab kernel's configuration for instance I, if it applies: as many
+// persistent CTAs (Lx Ly compute threads + a producer warp) as fit on the SMs.
+bool slab_cfg(ov_ctx* c, const Inst& I, DslashCfg* cfg) {
+  if (!(I.p == OP_F16 || I.p == OP_B16) || c->d_stencil_err == nullptr || !slab_lattice_ok(c->g)) return false;
+  const int per_sm = slab_ctas_per_sm(c->g);
+  if (per_sm <= 0) return false;
+  *cfg = DslashCfg{};
+  cfg->tpb = c->g.L[0] * c->g.L[1] + 32;
+  cfg->minb = 1;
+  cfg->lrec = 12;
+  cfg->slab = c->num_sms * per_sm;
+  cfg->err = c->d_stencil_err;
   return true;
 }
 
@@ -475,15 +508,19 @@ ov_status autotune(ov_ctx* c, Inst& I, const void* links_dev) {
   bool bad = false;
   const bool pinned = pinned_cfg(&pin, &bad);
   if (bad)
-    return fail(c, OV_ERR_INVALID, "OV_STENCIL must be \"tpb,minb,lrec[,rt]\" naming a compiled variant");
+    return fail(c, OV_ERR_INVALID,
+                "OV_STENCIL must be \"slab\" or \"tpb,minb,lrec[,rt]\" naming a compiled variant");
   DevBuf alt;  // the other 16-bit link layout
-  if (is16 && (!pinned || pin.lrec == 18)) {
+  if (is16 && (!pinned || (pin.slab == 0 && pin.lrec == 18))) {
     OV_CK(alt.ensure((size_t)link_bytes_per_site_dir(I.p, 18) * 4 * V));
     launch_pack_links(I.p, 18, c->g, links_dev, alt.p, c->st);
     OV_TRY(launched(c));
   }
   DslashCfg best_cfg;
-  if (pinned) {
+  if (pinned && pin.slab) {
+    DslashCfg sc;
+    if (slab_cfg(c, I, &sc)) best_cfg = sc;
+  } else if (pinned) {
     best_cfg = DslashCfg{pin.tpb, pin.minb, is16 ? pin.lrec : 12, 1};
     if (I.p == OP_F64 && pin.rt != 1) best_cfg.rt = 1;
   } else if (V >= 4096) {
@@ -510,6 +547,15 @@ ov_status autotune(ov_ctx* c, Inst& I, const void* links_dev) {
             best_cfg = cfg;
           }
         }
+    }
+    DslashCfg sc;
+    if (slab_cfg(c, I, &sc)) {
+      float ms = 0.f;
+      OV_TRY(time_variant(c, I, sc, I.links.p, 1, buf, e0, e1, &ms));
+      if (ms < best) {
+        best = ms;
+        best_cfg = sc;
+      }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -538,10 +584,10 @@ ov_status batch_cfg(ov_ctx* c, Inst& I, int nrhs, DslashCfg* out) {
   DslashCfg pin;
   bool bad = false;
   if (pinned_cfg(&pin, &bad)) {
-    best_cfg.tpb = pin.tpb;
-    best_cfg.minb = pin.minb;
-    best_cfg.rt = (I.p == OP_F64) ? 1 : pin.rt;
-    if (best_cfg.rt == 1 && best_cfg.minb == 1) best_cfg.minb = 2;
+    if (!pin.slab) {
+      best_cfg = DslashCfg{pin.tpb, pin.minb, I.cfg.lrec, (I.p == OP_F64) ? 1 : pin.rt};
+      if (best_cfg.rt == 1 && best_cfg.minb == 1) best_cfg.minb = 2;
+    }
   } else if (c->g.V >= 4096) {
     const int64_t V = c->g.V;
     DevBuf buf[4];
@@ -564,6 +610,15 @@ ov_status batch_cfg(ov_ctx* c, Inst& I, int nrhs, DslashCfg* out) {
           best_cfg = cfg;
         }
       }
+    DslashCfg sc;
+    if (I.cfg.lrec == 12 && slab_cfg(c, I, &sc)) {
+      float ms = 0.f;
+      OV_TRY(time_variant(c, I, sc, I.links.p, nrhs, buf, e0, e1, &ms));
+      if (ms < best) {
+        best = ms;
+        best_cfg = sc;
+      }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     OV_CK(cudaStreamSynchronize(c->st));
@@ -647,6 +702,15 @@ ov_status ov_create(ov_ctx** ctx, const int dims[4], const void* links, ov_prec 
       cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (c->num_sms <= 0) c->num_sms = 148;
   }
+  // flag of the slab stencil (without it the slab kernel is not used)
+  if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_stencil_err), sizeof(int), cudaHostAllocMapped) == cudaSuccess) {
+    *c->h_stencil_err = 0;
+    if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->d_stencil_err), c->h_stencil_err, 0) != cudaSuccess)
+      c->d_stencil_err = nullptr;
+  } else {
+    c->h_stencil_err = nullptr;
+  }
+  cudaGetLastError();
   const void* dl = nullptr;
   ov_status s = stage_in(c, c->stage_links, links, (size_t)V * 4 * 9 * 16, &dl);
   if (s == OV_OK) s = init_inst(c, c->hi, OP_F64, dl);
@@ -683,6 +747,7 @@ ov_status ov_destroy(ov_ctx* c) {
                     &c->o_x, &c->o_r, &c->o_rhs, &c->o_q})
     b->release();
   if (c->h_scalars) cudaFreeHost(c->h_scalars);
+  if (c->h_stencil_err) cudaFreeHost(c->h_stencil_err);
   delete c;
   return OV_OK;
 }
@@ -892,6 +957,7 @@ ov_status ov_get_stats(const ov_ctx* c, ov_stats* out) {
   out->stencil_tpb = I.cfg.tpb;
   out->stencil_minb = I.cfg.minb;
   out->stencil_lrec = (I.p == OP_F64) ? 18 : I.cfg.lrec;
+  out->stencil_slab = I.cfg.slab;
   return OV_OK;
 }
 

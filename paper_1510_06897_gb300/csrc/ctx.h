@@ -77,6 +77,8 @@ struct ov_ctx {
   DevBuf o_x, o_r, o_rhs, o_q;  // FP64 outer-solver vectors
   double* h_scalars = nullptr;  // pinned
   int h_scalars_n = 0;
+  int* h_stencil_err = nullptr;  // mapped pinned flag of the slab stencil (device view d_stencil_err)
+  int* d_stencil_err = nullptr;
   // solver controls
   double inner_tol = 1e-5;
   int max_outer = 30;

@@ -1,8 +1,27 @@
 // Stencil dispatch: picks the per-precision launcher compiled in
 // dslash_f64.cu / dslash_f32.cu / dslash_f16.cu / dslash_b16.cu.
-#include "dslash_kernel.cuh"
+#include "dslash_slab.cuh"
 
 namespace ov {
+
+bool slab_lattice_ok(const LatticeH& g) { return slab_supported(g); }
+
+int slab_ctas_per_sm(const LatticeH& g) {
+  if (!slab_supported(g)) return 0;
+  const int P = g.L[0] * g.L[1];
+  const size_t smem = slab::slab_smem_bytes(P);
+  auto kern = slab::k_dslash_slab<F16, F16>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, P + 32, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
 
 L2Window& l2_window() {
   static L2Window w;

@@ -26,6 +26,7 @@
 //   t:  (1-g) psi = (h0, h1, -h0, -h1),     h = (p0 - p2, p1 - p3)
 //       (1+g) psi = (h0, h1,  h0,  h1),     h = (p0 + p2, p1 + p3)
 #pragma once
+#include <utility>
 #include "common.cuh"
 #include "internal.h"
 #include "spin.cuh"
@@ -98,14 +99,72 @@ __device__ __forceinline__ void hop_pair(int s, int n_f, int n_b, bool neg_f, bo
   }
 }
 
+// Epilogue scalars in the arithmetic type R, converted once on the host (a
+// per-thread FP64 conversion would occupy the slow FP64 pipe).
+template <class R>
 struct EpiDev {
   int wilson, g5_out;
-  double m_w, s1, c0, wz;
+  R diag, s1, c0, wz;  // diag = 4 - m_w
   const void* v[3];
-  double w[3];
+  R w[3];
   const void* z;
   const void* y;
 };
+
+// Epilogue of one site and right-hand side (fields at byte offsets off / ooff):
+// r = D_W x or K x from the hop sum acc, then
+// out = c0 y + G(s1 r + sum_j w_j v_j + wz z).
+template <class ST, class OT, class R>
+__device__ __forceinline__ void epilogue(const EpiDev<R>& e, const char* in, char* out, int s, int V, long long off,
+                                         long long ooff, const Spinor<R>& acc) {
+  Spinor<R> xs;
+  load_spinor_as<ST, R>(in + off, s, V, xs);
+  const R half = R(0.5);
+  Spinor<R> r;
+  if (e.wilson) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) r.c[k] = R(4) * xs.c[k] - half * acc.c[k];
+  } else {
+    const R diag = e.diag;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      cplx<R> v = diag * xs.c[k] - half * acc.c[k];
+      r.c[k] = (k < 6) ? v : R(-1) * v;
+    }
+  }
+  const R s1 = e.s1;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) r.c[k] = s1 * r.c[k];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    if (e.v[j] != nullptr) {
+      Spinor<R> vj;
+      load_spinor_as<ST, R>(static_cast<const char*>(e.v[j]) + off, s, V, vj);
+      const R wj = e.w[j];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) r.c[k] = r.c[k] + wj * vj.c[k];
+    }
+  }
+  if (e.z != nullptr) {
+    Spinor<R> zv;
+    load_spinor_as<OT, R>(static_cast<const char*>(e.z) + ooff, s, V, zv);
+    const R wz = e.wz;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) r.c[k] = r.c[k] + wz * zv.c[k];
+  }
+  if (e.g5_out) {
+#pragma unroll
+    for (int k = 6; k < 12; ++k) r.c[k] = R(-1) * r.c[k];
+  }
+  if (e.y != nullptr) {
+    Spinor<R> yv;
+    load_spinor_as<OT, R>(static_cast<const char*>(e.y) + ooff, s, V, yv);
+    const R c0 = e.c0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) r.c[k] = r.c[k] + c0 * yv.c[k];
+  }
+  store_spinor_as<OT, R>(out + ooff, s, V, r);
+}
 
 struct Geo {
   int L[4];
@@ -121,7 +180,7 @@ struct Geo {
 // register allocator (1: no cap, 2: <= 128 registers, 3: <= 80, 4: <= 64).
 template <class LT, int LREC, class ST, class OT, int MINB, int RT>
 __global__ void __launch_bounds__(256, MINB) k_dslash(Geo g, const void* __restrict__ links,
-                                                      const char* __restrict__ in, char* out, EpiDev e,
+                                                      const char* __restrict__ in, char* out, EpiDev<typename Store<ST>::R> e,
                                                       long long rhs_bytes, long long out_rhs_bytes, int nrhs) {
   using R = typename Store<ST>::R;
   const int xy = blockIdx.x * blockDim.x + threadIdx.x;
@@ -161,55 +220,8 @@ __global__ void __launch_bounds__(256, MINB) k_dslash(Geo g, const void* __restr
 #pragma unroll
   for (int rr = 0; rr < RT; ++rr) {
     if (rr >= nv) break;
-    const long long off = (long long)(r0 + rr) * rhs_bytes;
-    const long long ooff = (long long)(r0 + rr) * out_rhs_bytes;
-    Spinor<R> xs;
-    load_spinor_as<ST, R>(in + off, s, V, xs);
-    const R half = R(0.5);
-    Spinor<R> r;
-    if (e.wilson) {
-#pragma unroll
-      for (int k = 0; k < 12; ++k) r.c[k] = R(4) * xs.c[k] - half * acc[rr].c[k];
-    } else {
-      const R diag = R(4.0 - e.m_w);
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        cplx<R> v = diag * xs.c[k] - half * acc[rr].c[k];
-        r.c[k] = (k < 6) ? v : R(-1) * v;
-      }
-    }
-    const R s1 = R(e.s1);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) r.c[k] = s1 * r.c[k];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      if (e.v[j] != nullptr) {
-        Spinor<R> vj;
-        load_spinor_as<ST, R>(static_cast<const char*>(e.v[j]) + off, s, V, vj);
-        const R wj = R(e.w[j]);
-#pragma unroll
-        for (int k = 0; k < 12; ++k) r.c[k] = r.c[k] + wj * vj.c[k];
-      }
-    }
-    if (e.z != nullptr) {
-      Spinor<R> zv;
-      load_spinor_as<OT, R>(static_cast<const char*>(e.z) + ooff, s, V, zv);
-      const R wz = R(e.wz);
-#pragma unroll
-      for (int k = 0; k < 12; ++k) r.c[k] = r.c[k] + wz * zv.c[k];
-    }
-    if (e.g5_out) {
-#pragma unroll
-      for (int k = 6; k < 12; ++k) r.c[k] = R(-1) * r.c[k];
-    }
-    if (e.y != nullptr) {
-      Spinor<R> yv;
-      load_spinor_as<OT, R>(static_cast<const char*>(e.y) + ooff, s, V, yv);
-      const R c0 = R(e.c0);
-#pragma unroll
-      for (int k = 0; k < 12; ++k) r.c[k] = r.c[k] + c0 * yv.c[k];
-    }
-    store_spinor_as<OT, R>(out + ooff, s, V, r);
+    epilogue<ST, OT>(e, in, out, s, V, (long long)(r0 + rr) * rhs_bytes, (long long)(r0 + rr) * out_rhs_bytes,
+                     acc[rr]);
   }
 }
 
@@ -222,34 +234,35 @@ inline Geo make_geo(const LatticeH& gh) {
   return g;
 }
 
-inline EpiDev make_epi(const EpiArgs& ea) {
-  EpiDev e;
+template <class R>
+inline EpiDev<R> make_epi(const EpiArgs& ea) {
+  EpiDev<R> e;
   e.wilson = ea.wilson;
   e.g5_out = ea.g5_out;
-  e.m_w = ea.m_w;
-  e.s1 = ea.s1;
-  e.c0 = ea.c0;
-  e.wz = ea.wz;
+  e.diag = R(4.0 - ea.m_w);
+  e.s1 = R(ea.s1);
+  e.c0 = R(ea.c0);
+  e.wz = R(ea.wz);
   e.y = ea.y;
   e.z = ea.z;
   for (int j = 0; j < 3; ++j) {
     e.v[j] = ea.v[j];
-    e.w[j] = ea.w[j];
+    e.w[j] = R(ea.w[j]);
   }
   return e;
 }
 
-template <class LT, int LREC, class ST, class OT, int MINB, int RT>
-void launch_k(const LatticeH& gh, const void* links, const void* in, void* out, const EpiArgs& ea, int nrhs, int tpb,
-              cudaStream_t st) {
-  const Geo g = make_geo(gh);
-  const long long rb = (long long)Store<ST>::bytes_per_site * g.V, orb = (long long)Store<OT>::bytes_per_site * g.V;
-  dim3 grid((unsigned)((g.LxLy + tpb - 1) / tpb), (unsigned)(gh.L[2] * gh.L[3]), (unsigned)((nrhs + RT - 1) / RT));
+// Launches kern<<<grid, block, smem, st>>>(args...), with the persisting L2
+// window on the links when one is set for this links pointer.
+template <class... KA, class... A>
+void launch_windowed(void (*kern)(KA...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, const void* links,
+                     A&&... args) {
   const L2Window& w = l2_window();
   if (w.base != nullptr && w.base == links) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
-    cfg.blockDim = dim3(tpb);
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
@@ -260,12 +273,21 @@ void launch_k(const LatticeH& gh, const void* links, const void* in, void* out, 
     attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_dslash<LT, LREC, ST, OT, MINB, RT>, g, links, static_cast<const char*>(in),
-                       static_cast<char*>(out), make_epi(ea), rb, orb, nrhs);
+    cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
     return;
   }
-  k_dslash<LT, LREC, ST, OT, MINB, RT><<<grid, tpb, 0, st>>>(g, links, static_cast<const char*>(in),
-                                                              static_cast<char*>(out), make_epi(ea), rb, orb, nrhs);
+  kern<<<grid, block, smem, st>>>(std::forward<A>(args)...);
+}
+
+template <class LT, int LREC, class ST, class OT, int MINB, int RT>
+void launch_k(const LatticeH& gh, const void* links, const void* in, void* out, const EpiArgs& ea, int nrhs, int tpb,
+              cudaStream_t st) {
+  const Geo g = make_geo(gh);
+  const long long rb = (long long)Store<ST>::bytes_per_site * g.V, orb = (long long)Store<OT>::bytes_per_site * g.V;
+  dim3 grid((unsigned)((g.LxLy + tpb - 1) / tpb), (unsigned)(gh.L[2] * gh.L[3]), (unsigned)((nrhs + RT - 1) / RT));
+  launch_windowed(k_dslash<LT, LREC, ST, OT, MINB, RT>, grid, dim3(tpb), 0, st, links, g, links,
+                  static_cast<const char*>(in), static_cast<char*>(out), make_epi<typename Store<ST>::R>(ea), rb, orb,
+                  nrhs);
 }
 
 // Variant table: (minb, rt) pairs compiled for each storage combination.

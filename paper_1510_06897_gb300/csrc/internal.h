@@ -53,7 +53,14 @@ struct DslashCfg {
   int minb = 2;
   int lrec = 12;
   int rt = 1;  // right-hand sides per thread (each link loaded once for all of them)
+  int slab = 0;  // > 0: the slab kernel (16-bit storage, 12-real links) on this many persistent CTAs
+  int* err = nullptr;  // slab kernel: set to 1 (device-visible memory) if a bulk copy did not land in time
 };
+
+// Whether the slab kernel takes this lattice (Lx Ly a multiple of 32, at most 640).
+bool slab_lattice_ok(const LatticeH& g);
+// Resident slab CTAs per SM on this lattice (0: not available).
+int slab_ctas_per_sm(const LatticeH& g);
 
 // Optional L2 access-policy window (persisting) applied to stencil launches
 // whose links pointer is `base`.

@@ -48,6 +48,46 @@ def test_stencil_variants(pin, prec, variant):
     assert rel(got, want) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("dims,nrhs", [((8, 4, 5, 6), 3), ((8, 4, 6, 16), 4), ((32, 2, 2, 2), 1)])
+def test_slab_stencil(monkeypatch, prec, dims, nrhs):
+    """The slab kernel pinned: D_W and K on several right-hand sides, with more
+    (rhs, slice) items than CTAs in the second case (each CTA cycles through
+    both shared-memory buffers several times) and Lz = Lt = 2 in the third
+    (the +mu and -mu planes coincide)."""
+    monkeypatch.setenv("OV_STENCIL", "slab")
+    links = inputs.gauge_links(dims, seed=8011)
+    psi = inputs.gaussian_source(dims, seed=8012, nrhs=nrhs)
+    with Ctx(dims, dev(links), prec, antiperiodic_t=True) as c:
+        assert c.stats()["stencil_slab"] > 0
+        got_w = host(c.wilson(dev(psi)))
+        got_k = host(c.kernel(dev(psi)))
+    want_w = np.stack([wilson.wilson(links, p, True) for p in psi])
+    want_k = np.stack([wilson.kernel_k(links, p, antiperiodic_t=True) for p in psi])
+    assert rel(got_w, want_w) < TOL[prec]
+    assert rel(got_k, want_k) < TOL[prec]
+
+
+def test_slab_sign_and_overlap(monkeypatch):
+    """sign(K) and D[mu] through the slab kernel (every epilogue form of the
+    recurrence and the FP32 assembly), 8 x 4 x 4 x 6, order 24, undeflated."""
+    monkeypatch.setenv("OV_STENCIL", "slab")
+    dims = (8, 4, 4, 6)
+    links = inputs.gauge_links(dims, seed=8021)
+    psi = inputs.gaussian_source(dims, seed=8022, nrhs=2)
+    a, b, order, mu = 0.2, 6.6, 24, 0.1
+    cfg = overlap.SignConfig(chebyshev.coefficients(order, a, b), a, b)
+    want_s = np.stack([overlap.sign_apply(links, p, cfg) for p in psi])
+    want_d = np.stack([overlap.overlap(links, p, mu, cfg) for p in psi])
+    with Ctx(dims, dev(links), "fp16") as c:
+        assert c.stats()["stencil_slab"] > 0
+        c.sign_config(order, a, b)
+        got_s = host(c.sign(dev(psi)))
+        got_d = host(c.overlap(dev(psi), mu))
+    assert rel(got_s, want_s) < 1e-2
+    assert rel(got_d, want_d) < 1e-2
+
+
 def _random_orthonormal(dims, n, seed):
     rng = np.random.default_rng(seed)
     vol = inputs.volume(dims)
