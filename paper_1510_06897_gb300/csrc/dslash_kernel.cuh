@@ -37,63 +37,91 @@ namespace ov {
 template <class ST>
 constexpr bool kPacked16 = std::is_same<ST, F16>::value || std::is_same<ST, B16>::value;
 
-template <class LT, int LREC, class R>
-__device__ __forceinline__ void load_link_fmt(const void* p, int mu, int s, int V, SU3<R>& u) {
-  if constexpr (LREC == 18 && (std::is_same<LT, F16>::value || std::is_same<LT, B16>::value))
-    load_link16_full<LT>(p, mu, s, V, u);
-  else
-    load_link<LT, R>(p, mu, s, V, u);
+// Accumulation of one projected, multiplied hop: paired FP32 additions for
+// FP32 accumulators, scalar ones for FP64; sg is the sign of a t hop.
+template <int MU, int SIGN, class R>
+__device__ __forceinline__ void accumulate_hop(Spinor<R>& acc, const Half<R>& uh, R sg) {
+  if constexpr (std::is_same<R, float>::value) {
+    if constexpr (MU == 3) expand_add_t2<SIGN>(acc, uh, sg);
+    else expand_add2<MU, SIGN>(acc, uh);
+  } else {
+    if constexpr (MU == 3) expand_add_t<SIGN>(acc, uh, sg);
+    else expand_add<MU, SIGN>(acc, uh);
+  }
 }
 
 // Both hops of direction MU for site s and the RT right-hand sides of this
 // thread (fields rhs_bytes apart, the last nv of them valid): the link of
 // each hop is loaded (and rebuilt) once and applied to every right-hand side.
 // n_f / n_b are the neighbour indices; neg_f / neg_b flip the sign (-1
-// across an antiperiodic t boundary).
+// across an antiperiodic t boundary).  16-bit storage keeps the link and the
+// projected two-spinor as packed words whose halves feed the FP32 FMAs
+// directly (mul_u16 / mul_udag16).
 template <int MU, class LT, int LREC, class ST, int RT, class R>
 __device__ __forceinline__ void hop_pair(int s, int n_f, int n_b, bool neg_f, bool neg_b, int V, const void* links,
                                          const char* in, long long rhs_bytes, int nv, Spinor<R> (&acc)[RT]) {
-  {  // forward: (1 - gamma_mu) U_mu(s) x(s + mu^)
-    SU3<R> u;
-    load_link_fmt<LT, LREC, R>(links, MU, s, V, u);
+  const R sg_f = neg_f ? R(-1) : R(1), sg_b = neg_b ? R(-1) : R(1);  // used by the t hops only
+  if constexpr (kPacked16<ST>) {
+    static_assert(std::is_same<LT, ST>::value, "16-bit spinors come with 16-bit links of the same type");
+    {  // forward: (1 - gamma_mu) U_mu(s) x(s + mu^)
+      uint32_t uw[9];
+      load_link_words16<LT, LREC>(links, MU, s, V, uw);
 #pragma unroll
-    for (int r = 0; r < RT; ++r) {
-      if (r < nv) {
-        Half<R> h, uh;
-        if constexpr (kPacked16<ST>) {
-          uint32_t w[12];
+      for (int r = 0; r < RT; ++r) {
+        if (RT == 1 || r < nv) {
+          uint32_t w[12], hw[6];
           load_words16(in + r * rhs_bytes, n_f, V, w);
-          project16<MU, -1, ST>(w, h);
-        } else {
+          project16w<MU, -1, ST>(w, hw);
+          Half<float> uh;
+          mul_u16<ST>(uw, hw, uh);
+          accumulate_hop<MU, -1>(acc[r], uh, sg_f);
+        }
+      }
+    }
+    {  // backward: (1 + gamma_mu) U_mu(s - mu^)^dagger x(s - mu^)
+      uint32_t uw[9];
+      load_link_words16<LT, LREC>(links, MU, n_b, V, uw);
+#pragma unroll
+      for (int r = 0; r < RT; ++r) {
+        if (RT == 1 || r < nv) {
+          uint32_t w[12], hw[6];
+          load_words16(in + r * rhs_bytes, n_b, V, w);
+          project16w<MU, +1, ST>(w, hw);
+          Half<float> uh;
+          mul_udag16<ST>(uw, hw, uh);
+          accumulate_hop<MU, +1>(acc[r], uh, sg_b);
+        }
+      }
+    }
+  } else {
+    {  // forward: (1 - gamma_mu) U_mu(s) x(s + mu^)
+      SU3<R> u;
+      load_link<LT, R>(links, MU, s, V, u);
+#pragma unroll
+      for (int r = 0; r < RT; ++r) {
+        if (RT == 1 || r < nv) {  // RT = 1: every launched thread has its right-hand side
+          Half<R> h, uh;
           Spinor<R> p;
           load_spinor_as<ST, R>(in + r * rhs_bytes, n_f, V, p);
           project<MU, -1>(p, h);
+          mul_u(u, h, uh);
+          accumulate_hop<MU, -1>(acc[r], uh, sg_f);
         }
-        if (MU == 3 && neg_f) scale_half(h, R(-1));  // block-uniform: a block is one (z, t) slice
-        mul_u(u, h, uh);
-        expand_add<MU, -1>(acc[r], uh);
       }
     }
-  }
-  {  // backward: (1 + gamma_mu) U_mu(s - mu^)^dagger x(s - mu^)
-    SU3<R> u;
-    load_link_fmt<LT, LREC, R>(links, MU, n_b, V, u);
+    {  // backward: (1 + gamma_mu) U_mu(s - mu^)^dagger x(s - mu^)
+      SU3<R> u;
+      load_link<LT, R>(links, MU, n_b, V, u);
 #pragma unroll
-    for (int r = 0; r < RT; ++r) {
-      if (r < nv) {
-        Half<R> h, uh;
-        if constexpr (kPacked16<ST>) {
-          uint32_t w[12];
-          load_words16(in + r * rhs_bytes, n_b, V, w);
-          project16<MU, +1, ST>(w, h);
-        } else {
+      for (int r = 0; r < RT; ++r) {
+        if (RT == 1 || r < nv) {
+          Half<R> h, uh;
           Spinor<R> p;
           load_spinor_as<ST, R>(in + r * rhs_bytes, n_b, V, p);
           project<MU, +1>(p, h);
+          mul_udag(u, h, uh);
+          accumulate_hop<MU, +1>(acc[r], uh, sg_b);
         }
-        if (MU == 3 && neg_b) scale_half(h, R(-1));
-        mul_udag(u, h, uh);
-        expand_add<MU, +1>(acc[r], uh);
       }
     }
   }
@@ -219,7 +247,7 @@ __global__ void __launch_bounds__(256, MINB) k_dslash(Geo g, const void* __restr
 
 #pragma unroll
   for (int rr = 0; rr < RT; ++rr) {
-    if (rr >= nv) break;
+    if (RT > 1 && rr >= nv) break;
     epilogue<ST, OT>(e, in, out, s, V, (long long)(r0 + rr) * rhs_bytes, (long long)(r0 + rr) * out_rhs_bytes,
                      acc[rr]);
   }
