@@ -438,8 +438,40 @@ def extras(args, ctx, links_d, a, b, evals, evecs, psi, vol):
             "precision": args.prec, "seconds": dt, "iterations": it, "outer": st["outer_iterations"],
             "true_rel_resid": r, "fp64_estimate_seconds": 12 * 2 * solves[args.prec]["iterations"] * fp64_apply}
     res["solve_1e-10"] = solves
+    res["solve_16x16x16x32_fp32"] = solve_16_timing()
     res["gradient"] = gradient_timing()
     return res
+
+
+def solve_16_timing():
+    """The 16^3 x 32 FP32-operator workload: 20 eigenpairs from ov_eigs,
+    Chebyshev order 200, CG on D^dagger D at mu = 0.05 to a 1e-10 true residual
+    (time to solution, iterations, stencil launches; eigensolver timed apart)."""
+    import torch
+    from paper_1510_06897_gb300 import inputs
+    from paper_1510_06897_gb300.binding import Ctx, ov_eigs, ov_get_stats, ov_reset_stats, ov_solve
+    dims, n_ev, order, mu = (16, 16, 16, 32), 20, 200, 0.05
+    links = torch.from_numpy(inputs.gauge_links(dims, seed=1002)).cuda()
+    b_src = torch.from_numpy(inputs.gaussian_source(dims, seed=2002)).cuda()
+    evecs = torch.zeros((n_ev + 1, dims[3], dims[2], dims[1], dims[0], 4, 3), dtype=torch.complex128, device="cuda")
+    with Ctx(dims, links, "fp32") as c:
+        t0 = time.perf_counter()
+        evals, lmax = ov_eigs(c.handle, n_ev + 1, 2e-5, 3000, evecs)  # dense low band, |lambda| 0.531..0.536
+        torch.cuda.synchronize()
+        t_eigs = time.perf_counter() - t0
+        a, b = float(abs(evals[n_ev])), float(lmax)
+        c.sign_config(order, a, b, evals[:n_ev], evecs[:n_ev].contiguous())
+        x = torch.empty_like(b_src)
+        ov_reset_stats(c.handle)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it, r = ov_solve(c.handle, mu, 1e-10, 20000, b_src, x, 1, allow_not_converged=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st = ov_get_stats(c.handle)
+    return {"seconds": dt, "iterations": it, "outer": st["outer_iterations"], "true_rel_resid": r,
+            "stencil_launches": st["dslash_launches"], "mu": mu, "order": order, "n_ev": n_ev,
+            "interval": [a, b], "eigs_seconds": t_eigs}
 
 
 def gradient_timing():
