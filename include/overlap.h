@@ -174,10 +174,14 @@ ov_status ov_eigs(ov_ctx* ctx, int n_ev, double tol, int max_iter, double* evals
 ov_status ov_sign_poly_grad(ov_ctx* ctx, int order, double lo, double hi, const void* chi, void* grad_links,
                             ov_dtype dtype);
 
-/* Profiling of the stencil kernel: when on != 0, every stencil launch is
- * bracketed by CUDA events on the context stream and its device time is added
- * to ov_stats.dslash_ms (read back whenever a call synchronises).  Off by
- * default; costs two event records per launch. */
+/* Profiling of the stencil kernel with CUDA events on the context stream;
+ * device time is added to ov_stats.dslash_ms and the number of stencil
+ * launches it covers to ov_stats.dslash_timed (read back whenever a call
+ * synchronises).  on = 1: an event pair around every stencil launch (exact
+ * per launch, but the event records slow a sign apply by a few percent);
+ * on = 2: one pair around the 2N back-to-back stencil launches of each
+ * Chebyshev recurrence (their summed time including the short gaps between
+ * them; other stencil launches are not timed); 0: off (default). */
 ov_status ov_set_profiling(ov_ctx* ctx, int on);
 
 ov_status ov_get_stats(const ov_ctx* ctx, ov_stats* out);

@@ -222,7 +222,8 @@ def ov_wilson_noalloc(dims, links, inp, out, nrhs, antiperiodic_t=False, stream=
 
 
 def ov_set_profiling(ctx, on):
-    return _check(lib().ov_set_profiling(ctx, int(bool(on))), ctx)
+    """on: 0 off, 1 (or True) every stencil launch, 2 the recurrence as one bracket (see overlap.h)."""
+    return _check(lib().ov_set_profiling(ctx, 2 if on == 2 else int(bool(on))), ctx)
 
 
 def ov_reset_stats(ctx):

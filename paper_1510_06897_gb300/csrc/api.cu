@@ -94,7 +94,7 @@ void prof_collect(ov_ctx* c) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, c->evs[i], c->evs[i + 1]) == cudaSuccess) {
       c->stats.dslash_ms += ms;
-      c->stats.dslash_timed++;
+      c->stats.dslash_timed += c->ev_count[i / 2];
     } else {
       cudaGetLastError();
     }
@@ -102,28 +102,36 @@ void prof_collect(ov_ctx* c) {
   c->ev_used = 0;
 }
 
+ov_status prof_open(ov_ctx* c) {
+  while (c->evs.size() < c->ev_used + 2) {
+    cudaEvent_t ev;
+    OV_CK(cudaEventCreate(&ev));
+    c->evs.push_back(ev);
+  }
+  if (c->ev_count.size() < c->evs.size() / 2) c->ev_count.resize(c->evs.size() / 2);
+  OV_CK(cudaEventRecord(c->evs[c->ev_used], c->st));
+  return OV_OK;
+}
+
+ov_status prof_close(ov_ctx* c, int n) {
+  OV_CK(cudaEventRecord(c->evs[c->ev_used + 1], c->st));
+  c->ev_count[c->ev_used / 2] = n;
+  c->ev_used += 2;
+  return OV_OK;
+}
+
 ov_status batch_cfg(ov_ctx* c, Inst& I, int nrhs, DslashCfg* out);
 
 ov_status dslash(ov_ctx* c, Inst& I, OpPrec out_prec, const void* in, void* out, const EpiArgs& e, int nrhs) {
   DslashCfg cfg;
   OV_TRY(batch_cfg(c, I, nrhs, &cfg));
-  if (c->prof) {
-    while (c->evs.size() < c->ev_used + 2) {
-      cudaEvent_t ev;
-      OV_CK(cudaEventCreate(&ev));
-      c->evs.push_back(ev);
-    }
-    OV_CK(cudaEventRecord(c->evs[c->ev_used], c->st));
-  }
+  if (c->prof == 1) OV_TRY(prof_open(c));
   if (!launch_dslash(I.p, out_prec, cfg, c->g, I.links.p, in, out, e, nrhs, c->st))
     return fail(c, OV_ERR_CUDA, "stencil variant not compiled");
   c->stats.dslash_launches++;
   ov_status s = launched(c);
   if (s != OV_OK) return s;
-  if (c->prof) {
-    OV_CK(cudaEventRecord(c->evs[c->ev_used + 1], c->st));
-    c->ev_used += 2;
-  }
+  if (c->prof == 1) OV_TRY(prof_close(c, 1));
   return OV_OK;
 }
 
@@ -275,6 +283,7 @@ ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kin
   };
   Vec b1{perp, cf[N]}, b2v{nullptr, 0.0};
   void* h = nullptr;
+  if (c->prof == 2) OV_TRY(prof_open(c));
   for (int k = N - 1; k >= 0; --k) {
     EpiArgs ek;
     ek.m_w = c->m_w;
@@ -295,6 +304,7 @@ ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kin
     b1 = Vec{dst, 1.0};
     h = dst;
   }
+  if (c->prof == 2) OV_TRY(prof_close(c, 2 * N));
 
   // S5: out = K h (= P(K) psi_perp) + d, with the overlap assembly (Eq. 1) fused:
   //   sign:   out = (K h + d) / scale
@@ -967,7 +977,7 @@ ov_status ov_set_profiling(ov_ctx* c, int on) {
     OV_CK(cudaStreamSynchronize(c->st));
     prof_collect(c);
   }
-  c->prof = on ? 1 : 0;
+  c->prof = (on == 2) ? 2 : (on ? 1 : 0);
   return OV_OK;
 }
 

@@ -84,9 +84,12 @@ struct ov_ctx {
   int max_outer = 30;
   ov_stats stats{};
   std::string err;
-  // stencil profiling (ov_set_profiling)
+  // stencil profiling (ov_set_profiling): 1 = an event pair around every
+  // stencil launch, 2 = one pair around each run of back-to-back stencil
+  // launches (the recurrence), with the number of launches it holds
   int prof = 0;
   std::vector<cudaEvent_t> evs;
+  std::vector<int> ev_count;  // stencil launches inside each recorded pair
   size_t ev_used = 0;
 
   Inst& op() { return prec == OV_FP64 ? hi : lo; }
@@ -113,6 +116,9 @@ ov_status check_dtype(ov_ctx* c, int nrhs, ov_dtype dt);
 ov_status dslash(ov_ctx* c, Inst& I, OpPrec out_prec, const void* in, void* out, const EpiArgs& e, int nrhs);
 // fold completed profiling event pairs into the stats (call after a stream sync)
 void prof_collect(ov_ctx* c);
+// profiling mode 2: open / close an event pair around n back-to-back stencil launches
+ov_status prof_open(ov_ctx* c);
+ov_status prof_close(ov_ctx* c, int n);
 // out (storage I.p) = stencil epilogue of K applied to `in` (see EpiArgs)
 ov_status k_step(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, const EpiArgs& e);
 ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kind kind, double mu, double scale);

@@ -166,3 +166,25 @@ def test_errors_and_state():
         assert e.value.status == 1
         c.sign_config(8, 0.5, 6.5)
         assert np.all(np.isfinite(host(c.sign(psi))))
+
+
+def test_profiling_modes():
+    """ov_set_profiling: mode 1 times every stencil launch (2N + 1 per sign
+    apply), mode 2 brackets the 2N recurrence launches with one event pair."""
+    from paper_1510_06897_gb300.binding import ov_reset_stats, ov_set_profiling
+    dims = (8, 8, 8, 8)
+    links = inputs.gauge_links(dims, seed=4701)
+    psi = dev(inputs.gaussian_source(dims, seed=4702))
+    order = 12
+    with Ctx(dims, dev(links), "fp16") as c:
+        c.sign_config(order, 0.5, 6.5)
+        c.sign(psi)
+        for mode, launches in ((1, 2 * order + 1), (2, 2 * order)):
+            ov_reset_stats(c.handle)
+            ov_set_profiling(c.handle, mode)
+            c.sign(psi)
+            c.sign(psi)
+            ov_set_profiling(c.handle, 0)
+            st = c.stats()
+            assert st["dslash_timed"] == 2 * launches, (mode, st["dslash_timed"])
+            assert st["dslash_ms"] > 0.0
