@@ -546,7 +546,7 @@ ov_status autotune(ov_ctx* c, Inst& I, const void* links_dev) {
     for (int lrec : {12, 18}) {
       if (!is16 && lrec == 18) continue;
       const void* links = (lrec == 18 && is16) ? alt.p : I.links.p;
-      for (int tpb : {128, 192, 256})
+      for (int tpb : {64, 96, 128, 192, 256})
         for (const auto& v : kVariants) {
           if (v[1] != 1) continue;
           DslashCfg cfg{tpb, v[0], is16 ? lrec : 12, 1};
@@ -609,7 +609,7 @@ ov_status batch_cfg(ov_ctx* c, Inst& I, int nrhs, DslashCfg* out) {
     OV_CK(cudaEventCreate(&e0));
     OV_CK(cudaEventCreate(&e1));
     float best = 1e30f;
-    for (int tpb : {128, 192, 256})
+    for (int tpb : {64, 96, 128, 192, 256})
       for (const auto& v : kVariants) {
         if (v[1] > nrhs || (I.p == OP_F64 && v[1] != 1)) continue;
         DslashCfg cfg{tpb, v[0], I.cfg.lrec, v[1]};
