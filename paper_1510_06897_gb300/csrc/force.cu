@@ -17,49 +17,61 @@
 
 namespace ov {
 
+template <class R>
 struct PairArgsDev {
   const char* u[kMaxForcePairs];
   const char* v[kMaxForcePairs];
-  double w[kMaxForcePairs];
+  R w[kMaxForcePairs];  // weights in the arithmetic type, converted on the host
   int n;
 };
 
+// M += sum_k a_k b_k^dagger over the two components of spin-projected
+// two-spinors a, b (colour outer products).  With P = 1 -/+ gamma_mu,
+// P^dagger P = 2 P and the lower spins of P x are unit-phase copies of its
+// upper two (the projection table in spin.cuh), so
+//   sum_s v_s [P a]_s^dagger = 1/2 sum_s [P v]_s [P a]_s^dagger
+//                            = sum_{k=0,1} h_k(v) h_k(a)^dagger,
+// h the two-spinor of project<MU, SIGN>: 18 complex products instead of 36.
 template <class R>
-__device__ __forceinline__ void outer_acc(cplx<R> (&M)[9], const Spinor<R>& a, const Spinor<R>& b, R w) {
-  // M += w sum_s a_s b_s^dagger
+__device__ __forceinline__ void outer_acc2(cplx<R> (&M)[9], const Half<R>& a, const Half<R>& b) {
 #pragma unroll
-  for (int s = 0; s < 4; ++s)
+  for (int k = 0; k < 2; ++k)
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) M[3 * i + j] = M[3 * i + j] + w * cmulc(b.c[3 * s + j], a.c[3 * s + i]);
+      for (int j = 0; j < 3; ++j) M[3 * i + j] = M[3 * i + j] + cmulc(b.c[3 * k + j], a.c[3 * k + i]);
 }
 
 template <int MU, class T, class R>
 __device__ __forceinline__ void force_dir(const Lattice& g, const Coords& c, int64_t s, int64_t stride,
-                                          const void* links, const PairArgsDev& P, cplx<R>* G) {
+                                          const void* links, const PairArgsDev<R>& P, cplx<R>* G) {
   const int64_t V = g.V;
   const int64_t n = neighbour(g, c, s, MU, +1, stride);
   cplx<R> A[9], B[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) A[k] = B[k] = {R(0), R(0)};
   for (int p = 0; p < P.n; ++p) {
-    const R w = R(P.w[p]);
-    Spinor<R> u, pu, v;
+    const R w = P.w[p];
+    Spinor<R> x;
+    Half<R> hv, ha;
     // A += w v(x+mu) [(1 - g_mu) g5 u(x)]^dagger
-    load_spinor<T, R>(P.u[p], s, V, u);
+    load_spinor<T, R>(P.u[p], s, V, x);
 #pragma unroll
-    for (int k = 6; k < 12; ++k) u.c[k] = R(-1) * u.c[k];
-    project_full<MU, -1>(u, pu);
-    load_spinor<T, R>(P.v[p], n, V, v);
-    outer_acc(A, v, pu, w);
+    for (int k = 6; k < 12; ++k) x.c[k] = R(-1) * x.c[k];
+    project<MU, -1>(x, ha);
+    load_spinor<T, R>(P.v[p], n, V, x);
+    project<MU, -1>(x, hv);
+    scale_half(hv, w);
+    outer_acc2(A, hv, ha);
     // B += w v(x) [(1 + g_mu) g5 u(x+mu)]^dagger
-    load_spinor<T, R>(P.u[p], n, V, u);
+    load_spinor<T, R>(P.u[p], n, V, x);
 #pragma unroll
-    for (int k = 6; k < 12; ++k) u.c[k] = R(-1) * u.c[k];
-    project_full<MU, +1>(u, pu);
-    load_spinor<T, R>(P.v[p], s, V, v);
-    outer_acc(B, v, pu, w);
+    for (int k = 6; k < 12; ++k) x.c[k] = R(-1) * x.c[k];
+    project<MU, +1>(x, ha);
+    load_spinor<T, R>(P.v[p], s, V, x);
+    project<MU, +1>(x, hv);
+    scale_half(hv, w);
+    outer_acc2(B, hv, ha);
   }
   SU3<R> U;
   load_link<T, R>(links, MU, s, V, U);
@@ -82,8 +94,8 @@ __device__ __forceinline__ void force_dir(const Lattice& g, const Coords& c, int
 }
 
 template <class T>
-__global__ void __launch_bounds__(128) k_force_pairs(Lattice g, const void* __restrict__ links, PairArgsDev P,
-                                                     void* Gv) {
+__global__ void __launch_bounds__(128) k_force_pairs(Lattice g, const void* __restrict__ links,
+                                                     PairArgsDev<typename Store<T>::R> P, void* Gv) {
   using R = typename Store<T>::R;
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= g.V) return;
@@ -104,16 +116,24 @@ void launch_force_pairs(OpPrec p, const LatticeH& gh, const void* links, const F
   for (int i = 0; i < 4; ++i) g.L[i] = gh.L[i];
   g.V = gh.V;
   g.antiperiodic_t = gh.antiperiodic_t;
-  PairArgsDev P;
-  P.n = pairs.n;
-  for (int i = 0; i < pairs.n; ++i) {
-    P.u[i] = static_cast<const char*>(pairs.u[i]);
-    P.v[i] = static_cast<const char*>(pairs.v[i]);
-    P.w[i] = pairs.w[i];
-  }
+  auto args = [&](auto* P) {
+    P->n = pairs.n;
+    for (int i = 0; i < pairs.n; ++i) {
+      P->u[i] = static_cast<const char*>(pairs.u[i]);
+      P->v[i] = static_cast<const char*>(pairs.v[i]);
+      P->w[i] = static_cast<decltype(+P->w[0])>(pairs.w[i]);
+    }
+  };
   dim3 grid((unsigned)((g.V + 127) / 128), 4);
-  if (p == OP_F64) k_force_pairs<F64><<<grid, 128, 0, st>>>(g, links, P, G);
-  else k_force_pairs<F32><<<grid, 128, 0, st>>>(g, links, P, G);
+  if (p == OP_F64) {
+    PairArgsDev<double> P;
+    args(&P);
+    k_force_pairs<F64><<<grid, 128, 0, st>>>(g, links, P, G);
+  } else {
+    PairArgsDev<float> P;
+    args(&P);
+    k_force_pairs<F32><<<grid, 128, 0, st>>>(g, links, P, G);
+  }
 }
 
 // F = P_TA(G^dagger) -> complex128 AoS [4][V][3][3]
