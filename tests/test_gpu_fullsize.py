@@ -35,24 +35,53 @@ def test_stencil_full_size(links, prec, tol):
     assert rel(got, want) < tol
 
 
-@pytest.mark.parametrize("prec,tol_h,tol_inv", [("fp32", 1e-6, 1e-5), ("fp16", 2e-3, 2e-2)])
-def test_sign_full_size_properties(links, prec, tol_h, tol_inv):
-    """<phi, S psi> = <S phi, psi> (S Hermitian) and S(S psi) = psi up to the
-    Chebyshev error and storage rounding, order 256, 40 deflated pairs."""
+@pytest.fixture(scope="module")
+def eig40(links):
+    """The 40 deflated pairs (+ the 41st for the interval) from ov_eigs, once."""
     n_ev = 40
-    ld = dev(links)
     evecs = torch.zeros((n_ev + 1,) + SHAPE, dtype=torch.complex128, device="cuda")
-    with Ctx(DIMS, ld, "fp32") as c32:
+    with Ctx(DIMS, dev(links), "fp32") as c32:
         evals, lmax = ov_eigs(c32.handle, n_ev + 1, 2e-5, 300, evecs)
-    a, b = float(abs(evals[n_ev])), float(lmax)
+    return {"evals": evals[:n_ev].copy(), "evecs": evecs[:n_ev].contiguous(), "a": float(abs(evals[n_ev])),
+            "b": float(lmax)}
+
+
+@pytest.mark.parametrize("prec,tol_h,tol_inv", [("fp32", 1e-6, 1e-5), ("fp16", 2e-3, 2e-2)])
+def test_sign_full_size_properties(links, eig40, prec, tol_h, tol_inv):
+    """<phi, S psi> = <S phi, psi> (S Hermitian), S(S psi) = psi up to the
+    Chebyshev error and storage rounding, and <phi, D psi> = <D^dag phi, psi>
+    for the assembled overlap operator (Eq. 1), order 256, 40 deflated pairs."""
     phi = dev(inputs.gaussian_source(DIMS, seed=2004))
     psi = dev(inputs.gaussian_source(DIMS, seed=2005))
-    with Ctx(DIMS, ld, prec) as c:
-        c.sign_config(256, a, b, evals[:n_ev], evecs[:n_ev].contiguous())
+    mu = 0.02
+    with Ctx(DIMS, dev(links), prec) as c:
+        c.sign_config(256, eig40["a"], eig40["b"], eig40["evals"], eig40["evecs"])
         s_psi = c.sign(psi)
         s_phi = c.sign(phi)
         ss_psi = c.sign(s_psi)
+        d_psi = c.overlap(psi, mu)
+        dd_phi = c.overlap(phi, mu, dagger=True)
+    scale = np.linalg.norm(host(phi)) * np.linalg.norm(host(psi))
     lhs = torch.vdot(phi.flatten(), s_psi.flatten()).item()
     rhs = torch.vdot(s_phi.flatten(), psi.flatten()).item()
-    assert abs(lhs - rhs) < tol_h * np.linalg.norm(host(phi)) * np.linalg.norm(host(psi))
+    assert abs(lhs - rhs) < tol_h * scale
     assert rel(host(ss_psi), host(psi)) < tol_inv
+    lhs = torch.vdot(phi.flatten(), d_psi.flatten()).item()
+    rhs = torch.vdot(dd_phi.flatten(), psi.flatten()).item()
+    assert abs(lhs - rhs) < tol_h * scale
+
+
+def test_batched_point_sources_full_size(links, eig40):
+    """The 12 spin-colour point sources in one FP16 call (batched stencil,
+    tensor-core deflation projection) against 12 one-RHS calls (CUDA-core
+    projection): equal up to the projection's TF32x3 error carried through
+    FP16 storage."""
+    src = dev(inputs.point_sources(DIMS))
+    with Ctx(DIMS, dev(links), "fp16") as c:
+        c.sign_config(256, eig40["a"], eig40["b"], eig40["evals"], eig40["evecs"])
+        batched = host(c.sign(src))
+        assert c.stats()["tc_gemm_launches"] > 0
+        single = np.concatenate([host(c.sign(src[r:r + 1].contiguous())) for r in range(12)])
+    assert rel(batched, single) < 1e-3
+    for r in range(12):
+        assert rel(batched[r], single[r]) < 2e-3
