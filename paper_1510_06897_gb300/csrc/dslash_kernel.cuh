@@ -127,69 +127,62 @@ __device__ __forceinline__ void hop_pair(int s, int n_f, int n_b, bool neg_f, bo
   }
 }
 
-// Epilogue scalars in the arithmetic type R, converted once on the host (a
-// per-thread FP64 conversion would occupy the slow FP64 pipe).
+// Epilogue coefficients in the arithmetic type R, formed once on the host
+// (a per-thread FP64 conversion would occupy the slow FP64 pipe) with every
+// sign folded in: index [0] applies to spins 0, 1 and [1] to spins 2, 3.
+//   out = xa x + ha acc + sum_j w_j v_j + wz z + c0 y
+// equals c0 y + G5(s1 G (d x - acc / 2) + sum_j w_j v_j + wz z) with G =
+// gamma5 for K (1 for D_W), d = 4 - m_w (4 for D_W), G5 = gamma5 if g5_out,
+// and acc the hop sum.
 template <class R>
 struct EpiDev {
-  int wilson, g5_out;
-  R diag, s1, c0, wz;  // diag = 4 - m_w
+  R xa[2], ha[2];
+  R w[3][2];
+  R wz[2];
+  R c0;
   const void* v[3];
-  R w[3];
   const void* z;
   const void* y;
 };
 
-// Epilogue of one site and right-hand side (fields at byte offsets off / ooff):
-// r = D_W x or K x from the hop sum acc, then
-// out = c0 y + G(s1 r + sum_j w_j v_j + wz z).
+// Epilogue of one site and right-hand side (fields at byte offsets off / ooff).
 template <class ST, class OT, class R>
 __device__ __forceinline__ void epilogue(const EpiDev<R>& e, const char* in, char* out, int s, int V, long long off,
                                          long long ooff, const Spinor<R>& acc) {
   Spinor<R> xs;
   load_spinor_as<ST, R>(in + off, s, V, xs);
-  const R half = R(0.5);
   Spinor<R> r;
-  if (e.wilson) {
 #pragma unroll
-    for (int k = 0; k < 12; ++k) r.c[k] = R(4) * xs.c[k] - half * acc.c[k];
-  } else {
-    const R diag = e.diag;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      cplx<R> v = diag * xs.c[k] - half * acc.c[k];
-      r.c[k] = (k < 6) ? v : R(-1) * v;
-    }
+  for (int k = 0; k < 12; ++k) {
+    const int h = k < 6 ? 0 : 1;
+    r.c[k] = {fma_(e.xa[h], xs.c[k].re, e.ha[h] * acc.c[k].re), fma_(e.xa[h], xs.c[k].im, e.ha[h] * acc.c[k].im)};
   }
-  const R s1 = e.s1;
-#pragma unroll
-  for (int k = 0; k < 12; ++k) r.c[k] = s1 * r.c[k];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     if (e.v[j] != nullptr) {
       Spinor<R> vj;
       load_spinor_as<ST, R>(static_cast<const char*>(e.v[j]) + off, s, V, vj);
-      const R wj = e.w[j];
 #pragma unroll
-      for (int k = 0; k < 12; ++k) r.c[k] = r.c[k] + wj * vj.c[k];
+      for (int k = 0; k < 12; ++k) {
+        const R wj = e.w[j][k < 6 ? 0 : 1];
+        r.c[k] = {fma_(wj, vj.c[k].re, r.c[k].re), fma_(wj, vj.c[k].im, r.c[k].im)};
+      }
     }
   }
   if (e.z != nullptr) {
     Spinor<R> zv;
     load_spinor_as<OT, R>(static_cast<const char*>(e.z) + ooff, s, V, zv);
-    const R wz = e.wz;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) r.c[k] = r.c[k] + wz * zv.c[k];
-  }
-  if (e.g5_out) {
-#pragma unroll
-    for (int k = 6; k < 12; ++k) r.c[k] = R(-1) * r.c[k];
+    for (int k = 0; k < 12; ++k) {
+      const R wz = e.wz[k < 6 ? 0 : 1];
+      r.c[k] = {fma_(wz, zv.c[k].re, r.c[k].re), fma_(wz, zv.c[k].im, r.c[k].im)};
+    }
   }
   if (e.y != nullptr) {
     Spinor<R> yv;
     load_spinor_as<OT, R>(static_cast<const char*>(e.y) + ooff, s, V, yv);
-    const R c0 = e.c0;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) r.c[k] = r.c[k] + c0 * yv.c[k];
+    for (int k = 0; k < 12; ++k) r.c[k] = {fma_(e.c0, yv.c[k].re, r.c[k].re), fma_(e.c0, yv.c[k].im, r.c[k].im)};
   }
   store_spinor_as<OT, R>(out + ooff, s, V, r);
 }
@@ -264,19 +257,24 @@ inline Geo make_geo(const LatticeH& gh) {
 
 template <class R>
 inline EpiDev<R> make_epi(const EpiArgs& ea) {
+  const double g_lo = ea.wilson ? 1.0 : -1.0;  // G on spins 2, 3
+  const double o_lo = ea.g5_out ? -1.0 : 1.0;  // G5 on spins 2, 3
+  const double d = ea.wilson ? 4.0 : 4.0 - ea.m_w;
   EpiDev<R> e;
-  e.wilson = ea.wilson;
-  e.g5_out = ea.g5_out;
-  e.diag = R(4.0 - ea.m_w);
-  e.s1 = R(ea.s1);
-  e.c0 = R(ea.c0);
-  e.wz = R(ea.wz);
-  e.y = ea.y;
-  e.z = ea.z;
+  e.xa[0] = R(ea.s1 * d);
+  e.xa[1] = R(ea.s1 * d * g_lo * o_lo);
+  e.ha[0] = R(-0.5 * ea.s1);
+  e.ha[1] = R(-0.5 * ea.s1 * g_lo * o_lo);
   for (int j = 0; j < 3; ++j) {
     e.v[j] = ea.v[j];
-    e.w[j] = R(ea.w[j]);
+    e.w[j][0] = R(ea.w[j]);
+    e.w[j][1] = R(ea.w[j] * o_lo);
   }
+  e.z = ea.z;
+  e.wz[0] = R(ea.wz);
+  e.wz[1] = R(ea.wz * o_lo);
+  e.y = ea.y;
+  e.c0 = R(ea.c0);
   return e;
 }
 
