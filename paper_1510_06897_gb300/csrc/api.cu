@@ -463,7 +463,7 @@ ov_status time_variant(ov_ctx* c, Inst& I, const DslashCfg& cfg, const void* lin
 }
 
 // (minb, rt) pairs compiled for the stencil (see dslash_kernel.cuh).
-const int kVariants[][2] = {{2, 1}, {3, 1}, {4, 1}, {2, 2}, {3, 2}, {1, 4}, {2, 4}};
+const int kVariants[][2] = {{2, 1}, {3, 1}, {4, 1}, {2, 2}, {3, 2}, {1, 3}, {2, 3}, {1, 4}, {2, 4}, {1, 6}};
 
 // The environment variable OV_STENCIL="tpb,minb,lrec[,rt]" (e.g. "192,3,12")
 // skips the timing and pins one variant (used for reproducible profiles);

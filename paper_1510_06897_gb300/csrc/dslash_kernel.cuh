@@ -327,7 +327,7 @@ bool launch_variant(const DslashCfg& c, const LatticeH& g, const void* links, co
   }
   OV_V(2, 1) OV_V(3, 1) OV_V(4, 1)
   if constexpr (!std::is_same<ST, F64>::value) {
-    OV_V(2, 2) OV_V(3, 2) OV_V(1, 4) OV_V(2, 4)
+    OV_V(2, 2) OV_V(3, 2) OV_V(1, 3) OV_V(2, 3) OV_V(1, 4) OV_V(2, 4) OV_V(1, 6)
   }
 #undef OV_V
   return false;

@@ -15,7 +15,8 @@ from tests.oracle_fixtures import field_shape, small_problem
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [(128, 2, 1), (192, 3, 1), (256, 4, 1), (128, 2, 2), (192, 3, 2), (64, 1, 4), (256, 2, 4)]
+VARIANTS = [(128, 2, 1), (192, 3, 1), (256, 4, 1), (128, 2, 2), (192, 3, 2), (96, 1, 3), (128, 2, 3), (64, 1, 4),
+            (256, 2, 4), (64, 1, 6)]
 TOL = {"fp64": 1e-13, "fp32": 1e-6, "fp16": 2e-3, "bf16": 1.5e-2}
 
 
