@@ -18,7 +18,7 @@ def main(argv=None):
     import torch
 
     from . import inputs
-    from .binding import Ctx, ov_eigs, ov_get_stats, ov_sign_apply, ov_solve
+    from .binding import Ctx, ov_eigs, ov_get_stats, ov_reset_stats, ov_set_profiling, ov_sign_apply, ov_solve
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--lattice", default="24,24,24,48")
@@ -31,6 +31,9 @@ def main(argv=None):
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--solve", action="store_true")
     ap.add_argument("--mu", type=float, default=0.02)
+    ap.add_argument("--profile", action="store_true",
+                    help="time the recurrence's stencil launches with CUDA events (profiling mode 2) after one "
+                         "untimed apply, and print the average per launch")
     args = ap.parse_args(argv)
 
     dims = tuple(int(x) for x in args.lattice.split(","))
@@ -45,6 +48,11 @@ def main(argv=None):
     with Ctx(dims, links, args.prec) as c:
         c.sign_config(args.order, args.lo, args.hi, evals, evecs)
         out = torch.empty_like(psi)
+        if args.profile and not args.solve:
+            ov_sign_apply(c.handle, psi, out, args.nrhs)  # tunes the stencil shape for nrhs
+            torch.cuda.synchronize()
+            ov_reset_stats(c.handle)
+            ov_set_profiling(c.handle, 2)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.applies):
@@ -55,6 +63,12 @@ def main(argv=None):
                 ov_sign_apply(c.handle, psi, out, args.nrhs)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        if args.profile and not args.solve:
+            ov_set_profiling(c.handle, 0)
+            st = ov_get_stats(c.handle)
+            per = st["dslash_ms"] / max(1, st["dslash_timed"]) * 1e3
+            print(f"stencil: {per:.2f} us per launch ({per / args.nrhs:.2f} per RHS) over {st['dslash_timed']} "
+                  f"recurrence launches", flush=True)
         print(f"{args.applies} x {'solve' if args.solve else 'sign apply'} ({args.prec}, {args.lattice}, "
               f"order {args.order}, n_ev {args.n_ev}, nrhs {args.nrhs}): {dt / args.applies * 1e3:.2f} ms each; "
               f"stats {ov_get_stats(c.handle)}", flush=True)
