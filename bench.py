@@ -45,6 +45,29 @@ FALLBACK_HBM_GBS = 6800.0
 LINK_B = {"fp64": 4 * 144, "fp32": 4 * 48, "fp16": 4 * 24, "bf16": 4 * 24}
 SPIN_B = {"fp64": 192, "fp32": 96, "fp16": 48, "bf16": 48}
 VEC_B = {"fp64": 192, "fp32": 96, "fp16": 96, "bf16": 96}
+# bytes per site of one D_W / K application when each link is read once and the
+# spinor once in and once out (the stored layouts: FP64 18-real links, the others
+# reconstruct-12)
+MIN_B = {p: LINK_B[p] + 2 * SPIN_B[p] for p in LINK_B}
+# the no-reuse convention quoted for the paper's era (1440 B/site in FP32: the 8
+# neighbour spinors and links, the output and the diagonal term, no cache reuse),
+# scaled by the storage width
+NO_REUSE_B = {"fp64": 2880, "fp32": 1440, "fp16": 720, "bf16": 720}
+
+
+def stencil_metrics(prec, vol, launch_s, peak_gbs):
+    """The metric triple of one stencil launch of launch_s seconds: ncu DRAM GB/s
+    (committed capture, when it matches the sources), t_min / t at MIN_B, and the
+    effective GB/s under the no-reuse convention."""
+    traffic = ncu_traffic(prec)
+    t_min = MIN_B[prec] * vol / (peak_gbs * 1e9)
+    out = {"t_min_over_t": t_min / launch_s, "min_bytes_per_site": MIN_B[prec],
+           "effective_GBps_no_reuse": NO_REUSE_B[prec] * vol / launch_s / 1e9,
+           "no_reuse_bytes_per_site": NO_REUSE_B[prec]}
+    if traffic is not None:
+        out["dram_GBps_ncu_traffic"] = traffic * vol / launch_s / 1e9
+        out["dram_frac_ncu_traffic"] = out["dram_GBps_ncu_traffic"] / peak_gbs
+    return out
 
 
 def recurrence_bytes(prec, order, vol):
@@ -306,6 +329,7 @@ def main():
                 "algorithmic_bytes_per_launch": bytes_launch,
                 "avg_launch_us": dslash_ms_avg * 1e3, "peak_source": f"hbm_gbs of {peak_kind}",
                 "stencil_share_of_step": st["dslash_ms"] / elapsed_ms if world == 1 else None}
+    roofline.update(stencil_metrics(args.prec, vol, dslash_ms_avg * 1e-3, hbm))
 
     # end to end through the C ABI with host (pinned) buffers
     psi_h = psi.cpu().pin_memory()
@@ -375,6 +399,7 @@ def extras(args, ctx, links_d, a, b, evals, evecs, psi, vol):
         gbs = recurrence_bytes(prec, ORDER, vol) / (2 * ORDER) / (avg * 1e-3) / 1e9
         res["precisions"][prec] = {"applies_per_s": 1e3 / ms, "ms_per_apply": ms, "stencil_avg_us": avg * 1e3,
                                    "stencil_GBps": gbs, "stencil_frac_of_hbm": gbs / hbm}
+        res["precisions"][prec].update(stencil_metrics(prec, vol, avg * 1e-3, hbm))
     # batched: the 12 spin-colour point sources in one call (config of the
     # batched workload), per-RHS rate against the single-RHS rate above
     from paper_1510_06897_gb300 import inputs as _inp
