@@ -252,7 +252,7 @@ __device__ __forceinline__ void load_link(const void* p, int mu, int s, int V, S
 
 template <>
 __device__ __forceinline__ void load_link<F64, double>(const void* p, int mu, int s, int V, SU3<double>& u) {
-  const double2* q = static_cast<const double2*>(p) + mu * 9 * V;
+  const double2* q = static_cast<const double2*>(p) + (int64_t)mu * 9 * V;
 #pragma unroll
   for (int e = 0; e < 9; ++e) {
     double2 v = __ldg(q + e * V + s);
@@ -261,7 +261,7 @@ __device__ __forceinline__ void load_link<F64, double>(const void* p, int mu, in
 }
 template <>
 __device__ __forceinline__ void load_link<F32, float>(const void* p, int mu, int s, int V, SU3<float>& u) {
-  const float4* q = static_cast<const float4*>(p) + mu * 3 * V;
+  const float4* q = static_cast<const float4*>(p) + (int64_t)mu * 3 * V;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     float4 v = __ldg(q + c * V + s);
@@ -272,7 +272,7 @@ __device__ __forceinline__ void load_link<F32, float>(const void* p, int mu, int
 }
 template <class T>
 __device__ __forceinline__ void load_link16(const void* p, int mu, int s, int V, SU3<float>& u) {
-  const uint2* q = static_cast<const uint2*>(p) + mu * 3 * V;
+  const uint2* q = static_cast<const uint2*>(p) + (int64_t)mu * 3 * V;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     uint2 v = __ldg(q + c * V + s);
@@ -286,7 +286,7 @@ __device__ __forceinline__ void load_link16(const void* p, int mu, int s, int V,
 // direction at [(mu*5 + c)*V + s], the second half of chunk 4 unused.
 template <class T>
 __device__ __forceinline__ void load_link16_full(const void* p, int mu, int s, int V, SU3<float>& u) {
-  const uint2* q = static_cast<const uint2*>(p) + mu * 5 * V;
+  const uint2* q = static_cast<const uint2*>(p) + (int64_t)mu * 5 * V;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     uint2 v = __ldg(q + c * V + s);

@@ -267,7 +267,7 @@ __device__ __forceinline__ void reconstruct16(uint32_t (&uw)[9]) {
 // rebuilt by reconstruct16) or all 18 (layout of load_link16_full).
 template <class T, int LREC>
 __device__ __forceinline__ void load_link_words16(const void* p, int mu, int s, int V, uint32_t (&uw)[9]) {
-  const uint2* q = static_cast<const uint2*>(p) + mu * (LREC == 18 ? 5 : 3) * V;
+  const uint2* q = static_cast<const uint2*>(p) + (int64_t)mu * (LREC == 18 ? 5 : 3) * V;
 #pragma unroll
   for (int c = 0; c < (LREC == 18 ? 4 : 3); ++c) {
     const uint2 v = __ldg(q + c * V + s);
