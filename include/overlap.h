@@ -95,7 +95,8 @@ typedef struct {
  * plus the copy in `prec`).  m_w: Wilson mass of the kernel (1.5 in Sec. 2).
  * antiperiodic_t != 0: fermion boundary condition antiperiodic in t (periodic
  * otherwise).  cuda_stream: a cudaStream_t (NULL = legacy default stream).
- * Errors: OV_ERR_INVALID (null ctx/dims/links, any L < 2, bad prec),
+ * Errors: OV_ERR_INVALID (null ctx/dims/links, any L < 2, V > 2^27,
+ * Lz * Lt > 65535, bad prec),
  * OV_ERR_NOMEM, OV_ERR_CUDA.
  * The stencil's launch shape and (16-bit) link layout are autotuned here by
  * timing a few launches of each variant on this lattice; the environment

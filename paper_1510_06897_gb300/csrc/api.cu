@@ -691,6 +691,10 @@ ov_status ov_create(ov_ctx** ctx, const int dims[4], const void* links, ov_prec 
     g_create_error = "ov_create: lattice too large";
     return OV_ERR_INVALID;
   }
+  if ((int64_t)dims[2] * dims[3] > 65535) {  // the stencil grid's y dimension is one (z, t) slice each
+    g_create_error = "ov_create: Lz * Lt must be <= 65535";
+    return OV_ERR_INVALID;
+  }
   if (prec < OV_FP64 || prec > OV_MIXED_BF16) {
     g_create_error = "ov_create: unknown precision";
     return OV_ERR_INVALID;

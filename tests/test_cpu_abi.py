@@ -47,6 +47,17 @@ def test_create_rejects_bad_dims_before_device_work(lib, dims):
     assert "extent" in binding.ov_last_error(None)
 
 
+@pytest.mark.parametrize("dims,msg", [((2, 2, 256, 512), "Lz * Lt"), ((1024, 1024, 16, 16), "too large")])
+def test_create_rejects_oversize_lattices_before_device_work(lib, dims, msg):
+    """More (z, t) slices than the stencil grid's y dimension holds, or more
+    than 2^27 sites: rejected on the host (no device allocation, no GPU needed)."""
+    links = np.zeros((4, 1, 1, 1, 1, 3, 3), dtype=np.complex128)
+    with pytest.raises(binding.OverlapError) as e:
+        binding.ov_create(dims, links)
+    assert e.value.status == binding.OV_ERR_INVALID
+    assert msg in binding.ov_last_error(None)
+
+
 def test_create_rejects_bad_precision_and_null(lib):
     links = np.zeros((4, 2, 2, 2, 2, 3, 3), dtype=np.complex128)
     with pytest.raises(binding.OverlapError):
