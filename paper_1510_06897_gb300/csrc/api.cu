@@ -413,6 +413,7 @@ ov_status cg_inner(ov_ctx* c, Inst& I, const void* r0, void* e, int nrhs, double
 
 ov_status check_dtype(ov_ctx* c, int nrhs, ov_dtype dt) {
   if (nrhs < 1) return fail(c, OV_ERR_INVALID, "nrhs must be >= 1");
+  if (nrhs > 65535) return fail(c, OV_ERR_INVALID, "nrhs must be <= 65535 (one stencil grid slot each)");
   if (dt != OV_C128 && dt != OV_C64) return fail(c, OV_ERR_INVALID, "dtype must be OV_C128 or OV_C64");
   return OV_OK;
 }
