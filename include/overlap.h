@@ -23,9 +23,8 @@
  *   links    complex128 [4][V][3][3]: U_mu(s) on the link s -> s+mu^, mu = x,y,z,t,
  *              colour matrix row-major.  Must be SU(3) to rounding (rows 0 and 1
  *              are stored in FP32/FP16/BF16 operators, row 2 is rebuilt).
- *   spinors  complex128 (OV_C128) or complex64 (OV_C64) [nrhs][V][4][3]
- *            (1 <= nrhs <= 65535),
- *              [spin][colour] per site.
+ *   spinors  complex128 (OV_C128) or complex64 (OV_C64) [nrhs][V][4][3],
+ *              [spin][colour] per site; 1 <= nrhs <= 65535.
  *   evecs    complex128 [n_ev][V][4][3], orthonormal eigenvectors of K.
  *
  * Pointers: every vector / link / evec pointer may be a device pointer or a
