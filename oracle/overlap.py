@@ -19,7 +19,10 @@ are Hermitian.
 
 Pinned by: dense sign(K) within eps_cheb, exactness on deflated modes,
 literal == projected, Ginsparg-Wilson bound, spectrum on the GW circle,
-gamma5 D gamma5 = D^dagger (tests/test_oracle_sign.py, tests/test_oracle_overlap.py).
+gamma5 D gamma5 = D^dagger (tests/test_oracle_sign.py, tests/test_oracle_overlap.py);
+the chiral-sector operator against P D^dagger D P built from dense matrices
+with the exact sign, and against it with the polynomial sign within the
+Chebyshev error (tests/test_oracle_chiral.py).
 """
 import numpy as np
 
@@ -102,3 +105,32 @@ def normal_op(links, psi, mu, cfg, m_w=M_W, antiperiodic_t=False):
     """D[mu]^dagger D[mu] psi."""
     return overlap_dag(links, overlap(links, psi, mu, cfg, m_w, antiperiodic_t),
                        mu, cfg, m_w, antiperiodic_t)
+
+
+def chiral_project(psi, chirality):
+    """P psi = (1 + chirality gamma5) / 2 psi: keeps spins 0, 1 (chirality +1)
+    or spins 2, 3 (chirality -1) of the chiral basis, gamma5 = diag(1, 1, -1, -1)."""
+    out = np.zeros_like(psi)
+    keep = slice(0, 2) if chirality > 0 else slice(2, 4)
+    out[..., keep, :] = psi[..., keep, :]
+    return out
+
+
+def chiral_normal_op(links, psi, mu, cfg, chirality, m_w=M_W, antiperiodic_t=False, sign=None):
+    """D[mu]^dagger D[mu] inside one chiral sector, written with a single sign
+    function application:
+
+      A psi = 1/4 [(1 + mu)^2 + (1 - mu)^2] P psi + chirality/2 (1 - mu^2) P S P psi.
+
+    From D^dagger D = 1/4 [(1+mu)^2 + (1-mu)^2 S^2 + (1-mu^2)(gamma5 S + S gamma5)]
+    (Eq. 1, S Hermitian): on chiral vectors the anticommutator becomes
+    2 chirality P S P, and S^2 = 1 turns the middle term into (1-mu)^2.  With
+    the polynomial S of Eq. 3, S^2 = 1 only up to the Chebyshev error, so A
+    differs from P D^dagger D P by that much; A itself is Hermitian and, for
+    |mu| < 1, positive definite on the sector.  sign: optional callable
+    replacing sign_apply (for pins with the exact dense sign)."""
+    p = chiral_project(psi, chirality)
+    s = sign(p) if sign is not None else sign_apply(links, p, cfg, m_w, antiperiodic_t)
+    c0 = 0.25 * ((1 + mu) ** 2 + (1 - mu) ** 2)
+    c1 = 0.5 * chirality * (1 - mu * mu)
+    return c0 * p + c1 * chiral_project(s, chirality)
