@@ -150,6 +150,23 @@ ov_status ov_overlap(ov_ctx* ctx, double mu, int dagger, const void* in, void* o
 ov_status ov_solve(ov_ctx* ctx, double mu, double tol, int maxit, const void* b, void* x, int nrhs,
                    ov_dtype dtype, int* iters, double* true_rel_resid);
 
+/* Chiral-sector solve (no separate counterpart in the paper: it follows from
+ * Eq. 1 and gamma5 = diag(1, 1, -1, -1)).  For a vector of one chirality,
+ * P psi = psi with P = (1 + chirality gamma5)/2,
+ *   D^dagger D psi = 1/4 [(1+mu)^2 + (1-mu)^2 S^2] psi + chirality/2 (1-mu^2) P S psi,
+ * S = sign(K); taking S^2 = 1 gives the sector operator
+ *   A = 1/4 [(1+mu)^2 + (1-mu)^2] P + chirality/2 (1-mu^2) P S P,
+ * which needs ONE sign(K) application per CG iteration instead of two.  With
+ * the polynomial S of Eq. 3, A differs from P D^dagger D P by the Chebyshev
+ * error (S^2 = 1 only to that accuracy).  Solves A x = P b (b is projected;
+ * x is returned with zero opposite-chirality components) until
+ * ||P b - A x|| / ||P b|| <= tol, recomputed with the FP64 operator; the same
+ * defect correction, iters and true_rel_resid as ov_solve.  D[mu]^{-1} P b is
+ * then D[mu]^dagger x.  chirality: +1 or -1; |mu| < 1.  Errors: OV_ERR_INVALID
+ * (bad chirality, |mu| >= 1, as ov_solve), OV_ERR_NOT_CONVERGED, OV_ERR_STATE. */
+ov_status ov_solve_chiral(ov_ctx* ctx, double mu, int chirality, double tol, int maxit, const void* b, void* x,
+                          int nrhs, ov_dtype dtype, int* iters, double* true_rel_resid);
+
 /* Inner-solver controls for the mixed-precision defect correction: relative
  * tolerance of each inner solve (default 1e-5) and the maximum number of FP64
  * outer steps (default 30). */

@@ -63,6 +63,7 @@ _SIGNATURES = {
     "ov_sign": [_vp, _i, _d, _d, ctypes.POINTER(_d), _vp, _i, _vp, _vp, _i, _i],
     "ov_overlap": [_vp, _d, _i, _vp, _vp, _i, _i],
     "ov_solve": [_vp, _d, _d, _i, _vp, _vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)],
+    "ov_solve_chiral": [_vp, _d, _i, _d, _i, _vp, _vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)],
     "ov_set_solver_params": [_vp, _d, _i],
     "ov_eigs": [_vp, _i, _d, _i, ctypes.POINTER(_d), _vp, ctypes.POINTER(_d)],
     "ov_sign_poly_grad": [_vp, _i, _d, _d, _vp, _vp, _i],
@@ -188,6 +189,17 @@ def ov_solve(ctx, mu, tol, maxit, b, x, nrhs, allow_not_converged=False):
     return it.value, res.value
 
 
+def ov_solve_chiral(ctx, mu, chirality, tol, maxit, b, x, nrhs, allow_not_converged=False):
+    """Chiral-sector solve A x = P b (see overlap.h); returns (iterations, true relative residual)."""
+    it = _i(0)
+    res = _d(0.0)
+    st = lib().ov_solve_chiral(ctx, float(mu), int(chirality), float(tol), int(maxit), _ptr(b), _ptr(x), int(nrhs),
+                               _dtype_code(b), ctypes.byref(it), ctypes.byref(res))
+    if not (allow_not_converged and st == OV_ERR_NOT_CONVERGED):
+        _check(st, ctx)
+    return it.value, res.value
+
+
 def ov_set_solver_params(ctx, inner_tol, max_outer):
     return _check(lib().ov_set_solver_params(ctx, float(inner_tol), int(max_outer)), ctx)
 
@@ -293,6 +305,11 @@ class Ctx:
     def solve(self, b, mu, tol=1e-10, maxit=5000):
         x = self._like(b)
         it, res = ov_solve(self.handle, mu, tol, maxit, b, x, b.shape[0])
+        return x, it, res
+
+    def solve_chiral(self, b, mu, chirality, tol=1e-10, maxit=5000):
+        x = self._like(b)
+        it, res = ov_solve_chiral(self.handle, mu, chirality, tol, maxit, b, x, b.shape[0])
         return x, it, res
 
     def stats(self):

@@ -310,17 +310,22 @@ ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kin
   //   sign:   out = (K h + d) / scale
   //   D:      out = (1+mu)/2 in + (1-mu)/2 gamma5 (K h + d) / scale
   //   D^dag:  out = (1+mu)/2 in + (1-mu)/2 (K h + d) / scale     (input was gamma5 in)
+  //   chiral: out = c0 in + c1 P (K h + d) / scale, c0 = [(1+mu)^2 + (1-mu)^2]/4,
+  //           c1 = +-(1 - mu^2)/2, P the projector on the input's chirality
   EpiArgs e;
   e.m_w = c->m_w;
-  const double f = (kind == K_SIGN ? 1.0 : 0.5 * (1.0 - mu)) / scale;
+  const bool chiral = (kind == K_CHI_P || kind == K_CHI_M);
+  const double c1 = 0.5 * (1.0 - mu * mu) * (kind == K_CHI_P ? 1.0 : -1.0);
+  const double f = (kind == K_SIGN ? 1.0 : chiral ? c1 : 0.5 * (1.0 - mu)) / scale;
   e.s1 = f;
   e.z = n_ev > 0 ? I.d.p : nullptr;
   e.wz = f;
   e.g5_out = (kind == K_OVL);
   if (kind != K_SIGN) {
     e.y = in;
-    e.c0 = 0.5 * (1.0 + mu);
+    e.c0 = chiral ? 0.25 * ((1.0 + mu) * (1.0 + mu) + (1.0 - mu) * (1.0 - mu)) : 0.5 * (1.0 + mu);
   }
+  if (chiral) e.keep_half = (kind == K_CHI_P) ? 0 : 1;
   OV_TRY(dslash(c, I, I.pv, h, out, e, nrhs));
   c->stats.sign_applies += nrhs;
   return OV_OK;
@@ -331,6 +336,11 @@ ov_status normal_apply(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, 
   OV_TRY(ensure_work(c, I, nrhs));
   OV_TRY(sign_core(c, I, in, I.tmp.p, nrhs, K_OVL, mu, scale));
   return sign_core(c, I, I.tmp.p, out, nrhs, K_OVL_DAG, mu, scale);
+}
+
+ov_status op_apply(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, double mu, double scale, int chirality) {
+  if (chirality == 0) return normal_apply(c, I, in, out, nrhs, mu, scale);
+  return sign_core(c, I, in, out, nrhs, chirality > 0 ? K_CHI_P : K_CHI_M, mu, scale);
 }
 
 ov_status dots(ov_ctx* c, OpPrec p, const void* a, const void* b, int64_t V, double2* out) {
@@ -352,7 +362,7 @@ ov_status norm2(ov_ctx* c, OpPrec p, const void* a, int64_t V, double* out) {
 // vectors in I.pv.  Stops when |r|/|r0| <= tol for every RHS (iterated
 // residual).  Returns the iteration count in *iters.
 ov_status cg_inner(ov_ctx* c, Inst& I, const void* r0, void* e, int nrhs, double mu, double tol, int maxit,
-                   int* iters) {
+                   int* iters, int chirality) {
   const int64_t V = c->g.V;
   const size_t vb = I.vbytes(V) * nrhs, v1 = I.vbytes(V);
   OV_CK(I.cx.ensure(vb));
@@ -381,7 +391,7 @@ ov_status cg_inner(ov_ctx* c, Inst& I, const void* r0, void* e, int nrhs, double
       if (!done[r]) rmax = std::max(rmax, std::sqrt(rr[r]));
     // keep 16-bit recurrence vectors at O(1) per component
     const double scale = is16 ? std::sqrt(24.0 * (double)V) / rmax : 1.0;
-    OV_TRY(normal_apply(c, I, I.cp.p, I.cq.p, nrhs, mu, scale));
+    OV_TRY(op_apply(c, I, I.cp.p, I.cq.p, nrhs, mu, scale, chirality));
     for (int r = 0; r < nrhs; ++r) {
       if (done[r]) continue;
       double2 pq;
@@ -872,8 +882,15 @@ ov_status ov_set_solver_params(ov_ctx* c, double inner_tol, int max_outer) {
   return OV_OK;
 }
 
-ov_status ov_solve(ov_ctx* c, double mu, double tol, int maxit, const void* b, void* x, int nrhs, ov_dtype dt,
-                   int* iters, double* true_rel_resid) {
+}  // extern "C"
+
+namespace ov {
+
+// CG on D^dagger D x = D^dagger b (chirality 0) or on the chiral-sector
+// operator A x = P b (chirality +-1), FP64 defect correction around the
+// inner solver of the context's precision.
+ov_status solve_core(ov_ctx* c, double mu, int chirality, double tol, int maxit, const void* b, void* x, int nrhs,
+                     ov_dtype dt, int* iters, double* true_rel_resid) {
   if (!c) return OV_ERR_INVALID;
   if (!b || !x) return fail(c, OV_ERR_INVALID, "null vector");
   if (!std::isfinite(mu) || !(tol > 0.0) || maxit < 1)
@@ -895,9 +912,17 @@ ov_status ov_solve(ov_ctx* c, double mu, double tol, int maxit, const void* b, v
   OV_CK(c->o_rhs.ensure(vb));
   OV_CK(c->o_q.ensure(vb));
   OV_CK(I.cx.ensure(iv1 * nrhs));
-  // rhs = D^dagger b with the FP64 operator
+  // rhs = D^dagger b with the FP64 operator, or P b (the FP64 layout keeps
+  // spinor component 3 spin + colour in chunk k: spins 2, 3 are chunks 6..11)
   OV_TRY(pack_input(c, H, b, nrhs, dt, H.xin.p));
-  OV_TRY(sign_core(c, H, H.xin.p, c->o_rhs.p, nrhs, K_OVL_DAG, mu, 1.0));
+  if (chirality == 0) {
+    OV_TRY(sign_core(c, H, H.xin.p, c->o_rhs.p, nrhs, K_OVL_DAG, mu, 1.0));
+  } else {
+    OV_CK(cudaMemcpyAsync(c->o_rhs.p, H.xin.p, vb, cudaMemcpyDeviceToDevice, c->st));
+    const size_t half = v1 / 2;
+    for (int r = 0; r < nrhs; ++r)
+      OV_CK(cudaMemsetAsync(c->o_rhs.c() + r * v1 + (chirality > 0 ? half : 0), 0, half, c->st));
+  }
   std::vector<double> rhs_n(nrhs), res(nrhs), rn(nrhs);
   for (int r = 0; r < nrhs; ++r) {
     OV_TRY(norm2(c, OP_F64, c->o_rhs.c() + r * v1, V, &rhs_n[r]));
@@ -931,7 +956,7 @@ ov_status ov_solve(ov_ctx* c, double mu, double tol, int maxit, const void* b, v
     if (c->prec != OV_FP64) inner = std::max(inner, c->inner_tol);
     inner = std::min(inner, 0.5);
     int it = 0;
-    ov_status s = cg_inner(c, I, I.xin.p, I.cx.p, nrhs, mu, inner, maxit - total, &it);
+    ov_status s = cg_inner(c, I, I.xin.p, I.cx.p, nrhs, mu, inner, maxit - total, &it, chirality);
     total += it;
     if (s != OV_OK && s != OV_ERR_NOT_CONVERGED) return s;
     for (int r = 0; r < nrhs; ++r) {
@@ -940,7 +965,7 @@ ov_status ov_solve(ov_ctx* c, double mu, double tol, int maxit, const void* b, v
     }
     c->stats.outer_iterations++;
     // true residual with the FP64 operator
-    OV_TRY(normal_apply(c, H, c->o_x.p, c->o_q.p, nrhs, mu, 1.0));
+    OV_TRY(op_apply(c, H, c->o_x.p, c->o_q.p, nrhs, mu, 1.0, chirality));
     launch_axpby(OP_F64, 1.0, c->o_rhs.p, -1.0, c->o_q.p, c->o_r.p, V, nrhs, c->st);
     OV_TRY(launched(c));
     for (int r = 0; r < nrhs; ++r) {
@@ -963,6 +988,23 @@ ov_status ov_solve(ov_ctx* c, double mu, double tol, int maxit, const void* b, v
   if (true_rel_resid) *true_rel_resid = mx;
   if (!ok) return fail(c, OV_ERR_NOT_CONVERGED, "solver stopped before reaching tol");
   return OV_OK;
+}
+
+}  // namespace ov
+
+extern "C" {
+
+ov_status ov_solve(ov_ctx* c, double mu, double tol, int maxit, const void* b, void* x, int nrhs, ov_dtype dt,
+                   int* iters, double* true_rel_resid) {
+  return solve_core(c, mu, 0, tol, maxit, b, x, nrhs, dt, iters, true_rel_resid);
+}
+
+ov_status ov_solve_chiral(ov_ctx* c, double mu, int chirality, double tol, int maxit, const void* b, void* x,
+                          int nrhs, ov_dtype dt, int* iters, double* true_rel_resid) {
+  if (!c) return OV_ERR_INVALID;
+  if (chirality != 1 && chirality != -1) return fail(c, OV_ERR_INVALID, "chirality must be +1 or -1");
+  if (!(std::fabs(mu) < 1.0)) return fail(c, OV_ERR_INVALID, "need |mu| < 1 (positive definite sector operator)");
+  return solve_core(c, mu, chirality, tol, maxit, b, x, nrhs, dt, iters, true_rel_resid);
 }
 
 ov_status ov_get_stats(const ov_ctx* c, ov_stats* out) {

@@ -50,7 +50,9 @@ struct Inst {
   }
 };
 
-enum Kind { K_SIGN, K_OVL, K_OVL_DAG };
+// K_CHI_P / K_CHI_M: the chiral-sector normal operator (input of that chirality):
+// out = 1/4 [(1+mu)^2 + (1-mu)^2] in +- 1/2 (1 - mu^2) P sign(K) in
+enum Kind { K_SIGN, K_OVL, K_OVL_DAG, K_CHI_P, K_CHI_M };
 
 }  // namespace ov
 
@@ -123,6 +125,8 @@ ov_status prof_close(ov_ctx* c, int n);
 ov_status k_step(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, const EpiArgs& e);
 ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kind kind, double mu, double scale);
 ov_status normal_apply(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, double mu, double scale);
+// D^dagger D (chirality 0) or the chiral-sector operator (chirality +-1)
+ov_status op_apply(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, double mu, double scale, int chirality);
 
 }  // namespace ov
 

@@ -275,6 +275,11 @@ inline EpiDev<R> make_epi(const EpiArgs& ea) {
   e.wz[1] = R(ea.wz * o_lo);
   e.y = ea.y;
   e.c0 = R(ea.c0);
+  if (ea.keep_half == 0 || ea.keep_half == 1) {  // chiral projection of everything but c0 y
+    const int h = 1 - ea.keep_half;
+    e.xa[h] = e.ha[h] = e.wz[h] = R(0);
+    for (int j = 0; j < 3; ++j) e.w[j][h] = R(0);
+  }
   return e;
 }
 

@@ -166,7 +166,7 @@ struct SlabEpi {
 };
 
 inline bool slab_epi(const EpiArgs& ea, SlabEpi* se) {
-  if (ea.s1 == 0.0) return false;
+  if (ea.s1 == 0.0 || ea.keep_half >= 0) return false;
   *se = SlabEpi{};
   se->nv = 0;
   const double gl = ea.wilson ? 1.0 : -1.0;

@@ -42,6 +42,7 @@ struct EpiArgs {
   double wz = 0.0;
   const void* y = nullptr;
   double c0 = 0.0;
+  int keep_half = -1;  // 0: spins 2, 3 of G5(...) set to zero (chirality +), 1: spins 0, 1; -1: none
 };
 
 // Launch shape and link layout of the stencil (chosen per operator by the
