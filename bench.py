@@ -461,6 +461,32 @@ def extras(args, ctx, links_d, a, b, evals, evecs, psi, vol):
         solves["batched_12_point_sources"] = {
             "precision": args.prec, "seconds": dt, "iterations": it, "outer": st["outer_iterations"],
             "true_rel_resid": r, "fp64_estimate_seconds": 12 * 2 * solves[args.prec]["iterations"] * fp64_apply}
+    # chiral point source (spin 0, colour 0 at the origin: chirality +1): D^-1 b
+    # from the chiral-sector solve (one sign apply per iteration) + one D^dagger,
+    # against the D^dagger D solve of the same source
+    from paper_1510_06897_gb300.binding import ov_overlap, ov_solve_chiral
+    src0 = src[0:1].contiguous()
+    chiral = {}
+    with Ctx(DIMS, links_d, args.prec) as c:
+        c.sign_config(ORDER, a, b, evals, evecs)
+        x = torch.empty_like(src0)
+        y = torch.empty_like(src0)
+        for name in ("chiral_sector", "normal_equations"):
+            ov_reset_stats(c.handle)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if name == "chiral_sector":
+                it, r = ov_solve_chiral(c.handle, MU, 1, 1e-10, 20000, src0, y, 1, allow_not_converged=True)
+                ov_overlap(c.handle, MU, 1, y, x, 1)            # D^-1 b = D^dagger A^-1 P b
+            else:
+                it, r = ov_solve(c.handle, MU, 1e-10, 20000, src0, x, 1, allow_not_converged=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            st = ov_get_stats(c.handle)
+            chiral[name] = {"seconds": dt, "iterations": it, "outer": st["outer_iterations"],
+                            "sign_applies": st["sign_applies"], "true_rel_resid": r}
+    chiral["speedup"] = chiral["normal_equations"]["seconds"] / chiral["chiral_sector"]["seconds"]
+    solves["chiral_point_source"] = chiral
     res["solve_1e-10"] = solves
     res["solve_16x16x16x32_fp32"] = solve_16_timing()
     res["gradient"] = gradient_timing()
