@@ -3,6 +3,7 @@
 // assembly), the overlap operator and the CG solver.  All arithmetic runs in
 // the kernels of dslash.cu / blas.cu; this file only sequences launches and
 // reads back FP64 scalars for the solver.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -553,7 +554,12 @@ ov_status autotune(ov_ctx* c, Inst& I, const void* links_dev) {
     cudaEvent_t e0, e1;
     OV_CK(cudaEventCreate(&e0));
     OV_CK(cudaEventCreate(&e1));
-    float best = 1e30f;
+    struct Cand {
+      float ms;
+      DslashCfg cfg;
+      const void* links;
+    };
+    std::vector<Cand> cands;
     for (int lrec : {12, 18}) {
       if (!is16 && lrec == 18) continue;
       const void* links = (lrec == 18 && is16) ? alt.p : I.links.p;
@@ -563,21 +569,29 @@ ov_status autotune(ov_ctx* c, Inst& I, const void* links_dev) {
           DslashCfg cfg{tpb, v[0], is16 ? lrec : 12, 1};
           float ms = 0.f;
           OV_TRY(time_variant(c, I, cfg, links, 1, buf, e0, e1, &ms));
-          if (ms < best) {
-            best = ms;
-            best_cfg = cfg;
-          }
+          cands.push_back({ms, cfg, links});
         }
     }
     DslashCfg sc;
     if (slab_cfg(c, I, &sc)) {
       float ms = 0.f;
       OV_TRY(time_variant(c, I, sc, I.links.p, 1, buf, e0, e1, &ms));
-      if (ms < best) {
-        best = ms;
-        best_cfg = sc;
-      }
+      cands.push_back({ms, sc, I.links.p});
     }
+    // the leaders are often within a few percent: time the best three again,
+    // interleaved, and keep each one's fastest run
+    std::sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) { return x.ms < y.ms; });
+    const size_t top = std::min<size_t>(3, cands.size());
+    for (int rep = 0; rep < 3; ++rep)
+      for (size_t k = 0; k < top; ++k) {
+        float ms = 0.f;
+        OV_TRY(time_variant(c, I, cands[k].cfg, cands[k].links, 1, buf, e0, e1, &ms));
+        cands[k].ms = std::min(cands[k].ms, ms);
+      }
+    size_t win = 0;
+    for (size_t k = 1; k < top; ++k)
+      if (cands[k].ms < cands[win].ms) win = k;
+    if (!cands.empty()) best_cfg = cands[win].cfg;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
