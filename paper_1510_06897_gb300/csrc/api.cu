@@ -1,16 +1,15 @@
-// C ABI of the overlap library: context, argument checks, host/device
-// staging, the sign(K) driver (deflation, Chebyshev recurrence, fused
-// assembly), the overlap operator and the CG solver.  All arithmetic runs in
-// the kernels of dslash.cu / blas.cu; this file only sequences launches and
-// reads back FP64 scalars for the solver.
+// C ABI of the overlap library: context creation and destruction, argument
+// checks and the entry points for D_W, K, sign(K), D[mu], statistics and
+// profiling.  The sign(K) driver lives in sign.cu, the solvers in solve.cu,
+// the stencil tuning in tune.cu and the shared helpers in ctx.cu; all
+// arithmetic runs in the kernels of dslash*.cu / blas.cu / eigs.cu.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
-
-#include <cstdlib>
 
 #include "ctx.h"
 
@@ -23,672 +22,6 @@ thread_local std::string g_create_error;
 namespace ov {
 // Message returned by ov_last_error(NULL) on this thread (context-free calls).
 void set_thread_error(const std::string& msg) { g_create_error = msg; }
-}  // namespace ov
-
-namespace ov {
-
-ov_status fail(ov_ctx* c, ov_status s, const std::string& msg) {
-  if (c) c->err = msg;
-  return s;
-}
-
-ov_status launched(ov_ctx* c, int n) {
-  c->stats.kernel_launches += n;
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(c, OV_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
-  return OV_OK;
-}
-
-bool is_device_ptr(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-// Device view of a caller input: the pointer itself, or a staged copy.
-ov_status stage_in(ov_ctx* c, DevBuf& buf, const void* p, size_t bytes, const void** out) {
-  if (is_device_ptr(p)) {
-    *out = p;
-    return OV_OK;
-  }
-  OV_CK(buf.ensure(bytes));
-  OV_CK(cudaMemcpyAsync(buf.p, p, bytes, cudaMemcpyHostToDevice, c->st));
-  *out = buf.p;
-  return OV_OK;
-}
-
-// Device destination for a caller output; finish_out copies it back if needed.
-ov_status stage_out(ov_ctx* c, void* p, size_t bytes, void** out, bool* staged) {
-  if (is_device_ptr(p)) {
-    *out = p;
-    *staged = false;
-    return OV_OK;
-  }
-  OV_CK(c->stage_out.ensure(bytes));
-  *out = c->stage_out.p;
-  *staged = true;
-  return OV_OK;
-}
-
-// After a stream sync: a slab stencil launch whose bulk copies did not land
-// in time left its flag set.
-ov_status stencil_status(ov_ctx* c) {
-  if (c->h_stencil_err && *static_cast<volatile int*>(c->h_stencil_err)) {
-    *c->h_stencil_err = 0;
-    return fail(c, OV_ERR_CUDA, "stencil: a shared-memory bulk copy did not complete in time");
-  }
-  return OV_OK;
-}
-
-ov_status finish_out(ov_ctx* c, void* host, size_t bytes, bool staged) {
-  if (staged) OV_CK(cudaMemcpyAsync(host, c->stage_out.p, bytes, cudaMemcpyDeviceToHost, c->st));
-  OV_CK(cudaStreamSynchronize(c->st));
-  prof_collect(c);
-  return stencil_status(c);
-}
-
-void prof_collect(ov_ctx* c) {
-  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, c->evs[i], c->evs[i + 1]) == cudaSuccess) {
-      c->stats.dslash_ms += ms;
-      c->stats.dslash_timed += c->ev_count[i / 2];
-    } else {
-      cudaGetLastError();
-    }
-  }
-  c->ev_used = 0;
-}
-
-ov_status prof_open(ov_ctx* c) {
-  while (c->evs.size() < c->ev_used + 2) {
-    cudaEvent_t ev;
-    OV_CK(cudaEventCreate(&ev));
-    c->evs.push_back(ev);
-  }
-  if (c->ev_count.size() < c->evs.size() / 2) c->ev_count.resize(c->evs.size() / 2);
-  OV_CK(cudaEventRecord(c->evs[c->ev_used], c->st));
-  return OV_OK;
-}
-
-ov_status prof_close(ov_ctx* c, int n) {
-  OV_CK(cudaEventRecord(c->evs[c->ev_used + 1], c->st));
-  c->ev_count[c->ev_used / 2] = n;
-  c->ev_used += 2;
-  return OV_OK;
-}
-
-ov_status batch_cfg(ov_ctx* c, Inst& I, int nrhs, DslashCfg* out);
-
-ov_status dslash(ov_ctx* c, Inst& I, OpPrec out_prec, const void* in, void* out, const EpiArgs& e, int nrhs) {
-  DslashCfg cfg;
-  OV_TRY(batch_cfg(c, I, nrhs, &cfg));
-  if (c->prof == 1) OV_TRY(prof_open(c));
-  if (!launch_dslash(I.p, out_prec, cfg, c->g, I.links.p, in, out, e, nrhs, c->st))
-    return fail(c, OV_ERR_CUDA, "stencil variant not compiled");
-  c->stats.dslash_launches++;
-  ov_status s = launched(c);
-  if (s != OV_OK) return s;
-  if (c->prof == 1) OV_TRY(prof_close(c, 1));
-  return OV_OK;
-}
-
-size_t iface_bytes(const LatticeH& g, int nrhs, ov_dtype dt) {
-  return (size_t)g.V * nrhs * 12 * (dt == OV_C128 ? 16 : 8);
-}
-
-ov_status ensure_scalars(ov_ctx* c, int n) {
-  if (c->h_scalars_n < n) {
-    if (c->h_scalars) cudaFreeHost(c->h_scalars);
-    c->h_scalars = nullptr;
-    c->h_scalars_n = 0;
-    OV_CK(cudaMallocHost(&c->h_scalars, sizeof(double2) * n));
-    c->h_scalars_n = n;
-  }
-  OV_CK(c->d_scalars.ensure(sizeof(double2) * n));
-  return OV_OK;
-}
-
-// Reads back n double2 values reduced from partial sums.
-ov_status read_reduced(ov_ctx* c, const double2* partial, int n, double2* out) {
-  OV_TRY(ensure_scalars(c, n));
-  launch_reduce_partials(partial, n, kReduceBlocks, c->d_scalars.as<double2>(), c->st);
-  OV_TRY(launched(c));
-  OV_CK(cudaMemcpyAsync(c->h_scalars, c->d_scalars.p, sizeof(double2) * n, cudaMemcpyDeviceToHost, c->st));
-  OV_CK(cudaStreamSynchronize(c->st));
-  prof_collect(c);
-  OV_TRY(stencil_status(c));
-  std::memcpy(out, c->h_scalars, sizeof(double2) * n);
-  return OV_OK;
-}
-
-ov_status ensure_work(ov_ctx* c, Inst& I, int nrhs) {
-  const int64_t V = c->g.V;
-  const size_t vb = I.vbytes(V) * nrhs, pb = I.pbytes(V) * nrhs;
-  OV_CK(I.xin.ensure(vb));
-  OV_CK(I.xout.ensure(vb));
-  OV_CK(I.d.ensure(vb));
-  OV_CK(I.tmp.ensure(vb));
-  OV_CK(I.perp.ensure(pb));
-  OV_CK(I.t.ensure(pb));
-  OV_CK(I.bA.ensure(pb));
-  OV_CK(I.bB.ensure(pb));
-  OV_CK(c->d_partial.ensure(sizeof(double2) * kReduceBlocks * (size_t)std::max(1, c->n_ev)));
-  OV_CK(c->d_c.ensure(sizeof(double2) * (size_t)std::max(1, c->n_ev) * nrhs));
-  return OV_OK;
-}
-
-// Chebyshev-Gauss interpolation of y^{-1/2} on [a^2, b^2] (Eq. 3 reading):
-// c_j = 2/(N+1) sum_k f(y_k) cos(j theta_k), theta_k = pi (k + 1/2)/(N + 1).
-std::vector<double> chebyshev_coefficients(int order, double a, double b) {
-  const int n1 = order + 1;
-  std::vector<double> f(n1), c(n1);
-  const double pi = 3.14159265358979323846;
-  for (int k = 0; k < n1; ++k) {
-    const double th = pi * (k + 0.5) / n1;
-    const double y = 0.5 * ((b * b - a * a) * std::cos(th) + b * b + a * a);
-    f[k] = 1.0 / std::sqrt(y);
-  }
-  for (int j = 0; j < n1; ++j) {
-    double s = 0.0;
-    for (int k = 0; k < n1; ++k) s += f[k] * std::cos(j * pi * (k + 0.5) / n1);
-    c[j] = 2.0 * s / n1;
-  }
-  return c;
-}
-
-// K applied to a recurrence vector: out (storage I.p) = s1 K in + sum w_j v_j.
-ov_status k_step(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, const EpiArgs& e) {
-  return dslash(c, I, I.p, in, out, e, nrhs);
-}
-
-// sign(K) / D[mu] / D[mu]^dagger on nrhs vectors in I.pv storage.
-// scale: the recurrence runs on scale * (input); results are unscaled in the
-// final epilogue (used to keep 16-bit storage in range).
-ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kind kind, double mu, double scale) {
-  if (!c->configured) return fail(c, OV_ERR_STATE, "sign(K) not configured: call ov_sign_config first");
-  OV_TRY(ensure_work(c, I, nrhs));
-  const int64_t V = c->g.V;
-  const size_t vb = I.vbytes(V), pb = I.pbytes(V);
-  const int g5in = (kind == K_OVL_DAG);
-  const int n_ev = c->n_ev;
-
-  // S3: deflation projection c_i = phi_i^dagger psi, psi_perp = psi - sum c_i phi_i,
-  //     d = sum sgn(lambda_i) c_i phi_i  (both scaled by `scale`).  Several
-  //     right-hand sides: one Gram launch reads every eigenvector once for all
-  //     of them (c stored [i][r]); one right-hand side: the projection kernel.
-  const bool batched = (n_ev > 0 && nrhs > 1 && n_ev <= gram_max_vectors() && nrhs <= gram_max_vectors());
-  if (batched) {
-    OV_CK(c->d_gram.ensure(sizeof(double2) * (size_t)n_ev * nrhs * kReduceBlocks));
-    const char* mode = std::getenv("OV_DEFL_GEMM");
-    const bool tc = I.pv == OP_F32 && n_ev <= tc_gram_max_rows() && nrhs <= tc_gram_max_rhs() &&
-                    !(mode && std::strcmp(mode, "cuda") == 0);
-    int nblk = kReduceBlocks;
-    if (tc) {
-      // tensor cores: one CTA per SM, TF32 x 3 split products
-      nblk = std::min(c->num_sms, kReduceBlocks);
-      OV_CK(c->d_err.ensure(sizeof(int)));
-      OV_CK(cudaMemsetAsync(c->d_err.p, 0, sizeof(int), c->st));
-      OV_CK(launch_tc_gram(I.evecs.p, n_ev, in, nrhs, V, g5in, c->d_gram.as<double2>(), nblk, c->d_err.as<int>(),
-                           c->st));
-      OV_TRY(launched(c));
-      c->stats.tc_gemm_launches++;
-      int herr = 0;
-      OV_CK(cudaMemcpyAsync(&herr, c->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-      OV_CK(cudaStreamSynchronize(c->st));
-      if (herr) return fail(c, OV_ERR_CUDA, "tensor-core projection: a bounded wait expired");
-    } else {
-      OV_CK(launch_gram(I.pv, I.evecs.p, n_ev, in, nrhs, V, c->d_gram.as<double2>(), kReduceBlocks, c->st, g5in));
-      OV_TRY(launched(c));
-    }
-    launch_reduce_partials(c->d_gram.as<double2>(), n_ev * nrhs, nblk, c->d_c.as<double2>(), c->st);
-    OV_TRY(launched(c));
-  }
-  if (batched && I.pv == OP_F32 && n_ev <= 128) {
-    launch_defl_combine_multi(I.p, c->g, I.evecs.p, n_ev, c->d_c.as<double2>(), nrhs, c->d_sgn.as<double>(), in,
-                              g5in, scale, I.perp.p, I.d.p, c->st);
-    OV_TRY(launched(c));
-  } else {
-    for (int r = 0; r < nrhs; ++r) {
-      const char* in_r = static_cast<const char*>(in) + r * vb;
-      double2* cr = batched ? c->d_c.as<double2>() + r : c->d_c.as<double2>() + (size_t)r * std::max(1, n_ev);
-      const int cstride = batched ? nrhs : 1;
-      if (n_ev > 0 && !batched) {
-        launch_defl_dot(I.pv, c->g, I.evecs.p, n_ev, in_r, g5in, c->d_partial.as<double2>(), c->st);
-        OV_TRY(launched(c));
-        launch_reduce_partials(c->d_partial.as<double2>(), n_ev, kReduceBlocks, cr, c->st);
-        OV_TRY(launched(c));
-      }
-      launch_defl_combine(I.pv, I.p, c->g, I.evecs.p, n_ev, cr, cstride, c->d_sgn.as<double>(), in_r, g5in, scale,
-                          I.perp.c() + r * pb, n_ev > 0 ? I.d.c() + r * vb : nullptr, c->st);
-      OV_TRY(launched(c));
-    }
-  }
-
-  // S4: backward (Clenshaw) recurrence for f_N(Z) psi_perp, Z = alpha K^2 + beta:
-  //   b_k = c_k psi_perp + 2 Z b_{k+1} - b_{k+2},  k = N-1 .. 1,  b_N = c_N psi_perp,
-  //   h   = (b_0 - b_2)/2 = c_0/2 psi_perp + Z b_1 - b_2.
-  // Each Z application is two stencil launches; the second carries the
-  // recurrence algebra in its epilogue.
-  const double a2 = c->a * c->a, b2 = c->b * c->b;
-  const double alpha = 2.0 / (b2 - a2), beta = -(b2 + a2) / (b2 - a2);
-  const std::vector<double>& cf = c->coef;
-  const int N = c->order;
-  void* perp = I.perp.p;
-  struct Vec {
-    void* p;
-    double s;
-  };
-  Vec b1{perp, cf[N]}, b2v{nullptr, 0.0};
-  void* h = nullptr;
-  if (c->prof == 2) OV_TRY(prof_open(c));
-  for (int k = N - 1; k >= 0; --k) {
-    EpiArgs ek;
-    ek.m_w = c->m_w;
-    OV_TRY(k_step(c, I, b1.p, I.t.p, nrhs, ek));  // t = K b1.p
-    void* dst = (b2v.p != nullptr && b2v.p != perp) ? b2v.p : (b1.p == I.bA.p ? I.bB.p : I.bA.p);
-    EpiArgs e;
-    e.m_w = c->m_w;
-    const double zs = (k > 0) ? 2.0 : 1.0;  // last step builds (b_0 - b_2)/2
-    e.s1 = zs * alpha * b1.s;
-    e.v[0] = b1.p;
-    e.w[0] = zs * beta * b1.s;
-    e.v[1] = b2v.p;
-    e.w[1] = -b2v.s;
-    e.v[2] = perp;
-    e.w[2] = (k > 0) ? cf[k] : 0.5 * cf[0];
-    OV_TRY(k_step(c, I, I.t.p, dst, nrhs, e));
-    b2v = b1;
-    b1 = Vec{dst, 1.0};
-    h = dst;
-  }
-  if (c->prof == 2) OV_TRY(prof_close(c, 2 * N));
-
-  // S5: out = K h (= P(K) psi_perp) + d, with the overlap assembly (Eq. 1) fused:
-  //   sign:   out = (K h + d) / scale
-  //   D:      out = (1+mu)/2 in + (1-mu)/2 gamma5 (K h + d) / scale
-  //   D^dag:  out = (1+mu)/2 in + (1-mu)/2 (K h + d) / scale     (input was gamma5 in)
-  //   chiral: out = c0 in + c1 P (K h + d) / scale, c0 = [(1+mu)^2 + (1-mu)^2]/4,
-  //           c1 = +-(1 - mu^2)/2, P the projector on the input's chirality
-  EpiArgs e;
-  e.m_w = c->m_w;
-  const bool chiral = (kind == K_CHI_P || kind == K_CHI_M);
-  const double c1 = 0.5 * (1.0 - mu * mu) * (kind == K_CHI_P ? 1.0 : -1.0);
-  const double f = (kind == K_SIGN ? 1.0 : chiral ? c1 : 0.5 * (1.0 - mu)) / scale;
-  e.s1 = f;
-  e.z = n_ev > 0 ? I.d.p : nullptr;
-  e.wz = f;
-  e.g5_out = (kind == K_OVL);
-  if (kind != K_SIGN) {
-    e.y = in;
-    e.c0 = chiral ? 0.25 * ((1.0 + mu) * (1.0 + mu) + (1.0 - mu) * (1.0 - mu)) : 0.5 * (1.0 + mu);
-  }
-  if (chiral) e.keep_half = (kind == K_CHI_P) ? 0 : 1;
-  OV_TRY(dslash(c, I, I.pv, h, out, e, nrhs));
-  c->stats.sign_applies += nrhs;
-  return OV_OK;
-}
-
-// out = D^dagger D in (vectors in I.pv), through I.tmp.
-ov_status normal_apply(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, double mu, double scale) {
-  OV_TRY(ensure_work(c, I, nrhs));
-  OV_TRY(sign_core(c, I, in, I.tmp.p, nrhs, K_OVL, mu, scale));
-  return sign_core(c, I, I.tmp.p, out, nrhs, K_OVL_DAG, mu, scale);
-}
-
-ov_status op_apply(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, double mu, double scale, int chirality) {
-  if (chirality == 0) return normal_apply(c, I, in, out, nrhs, mu, scale);
-  return sign_core(c, I, in, out, nrhs, chirality > 0 ? K_CHI_P : K_CHI_M, mu, scale);
-}
-
-ov_status dots(ov_ctx* c, OpPrec p, const void* a, const void* b, int64_t V, double2* out) {
-  launch_dot_partial(p, a, b, V, 1, c->d_partial.as<double2>(), c->st);
-  OV_TRY(launched(c));
-  return read_reduced(c, c->d_partial.as<double2>(), 1, out);
-}
-
-ov_status norm2(ov_ctx* c, OpPrec p, const void* a, int64_t V, double* out) {
-  launch_norm2_partial(p, a, V, 1, c->d_partial.as<double2>(), c->st);
-  OV_TRY(launched(c));
-  double2 r;
-  OV_TRY(read_reduced(c, c->d_partial.as<double2>(), 1, &r));
-  *out = r.x;
-  return OV_OK;
-}
-
-// CG on D^dagger D e = r0 for each RHS, with the operator of instance I;
-// vectors in I.pv.  Stops when |r|/|r0| <= tol for every RHS (iterated
-// residual).  Returns the iteration count in *iters.
-ov_status cg_inner(ov_ctx* c, Inst& I, const void* r0, void* e, int nrhs, double mu, double tol, int maxit,
-                   int* iters, int chirality) {
-  const int64_t V = c->g.V;
-  const size_t vb = I.vbytes(V) * nrhs, v1 = I.vbytes(V);
-  OV_CK(I.cx.ensure(vb));
-  OV_CK(I.cr.ensure(vb));
-  OV_CK(I.cp.ensure(vb));
-  OV_CK(I.cq.ensure(vb));
-  OV_TRY(ensure_work(c, I, nrhs));
-  OV_CK(cudaMemsetAsync(e, 0, vb, c->st));
-  OV_CK(cudaMemcpyAsync(I.cr.p, r0, vb, cudaMemcpyDeviceToDevice, c->st));
-  OV_CK(cudaMemcpyAsync(I.cp.p, r0, vb, cudaMemcpyDeviceToDevice, c->st));
-  std::vector<double> rr(nrhs), rr0(nrhs);
-  std::vector<char> done(nrhs, 0);
-  for (int r = 0; r < nrhs; ++r) {
-    OV_TRY(norm2(c, I.pv, I.cr.c() + r * v1, V, &rr[r]));
-    rr0[r] = rr[r];
-    if (rr0[r] == 0.0) done[r] = 1;
-  }
-  const bool is16 = (I.p == OP_F16 || I.p == OP_B16);
-  int it = 0;
-  for (; it < maxit; ++it) {
-    bool all = true;
-    for (int r = 0; r < nrhs; ++r) all = all && done[r];
-    if (all) break;
-    double rmax = 0.0;
-    for (int r = 0; r < nrhs; ++r)
-      if (!done[r]) rmax = std::max(rmax, std::sqrt(rr[r]));
-    // keep 16-bit recurrence vectors at O(1) per component
-    const double scale = is16 ? std::sqrt(24.0 * (double)V) / rmax : 1.0;
-    OV_TRY(op_apply(c, I, I.cp.p, I.cq.p, nrhs, mu, scale, chirality));
-    for (int r = 0; r < nrhs; ++r) {
-      if (done[r]) continue;
-      double2 pq;
-      OV_TRY(dots(c, I.pv, I.cp.c() + r * v1, I.cq.c() + r * v1, V, &pq));
-      if (!(pq.x > 0.0) || !std::isfinite(pq.x))
-        return fail(c, OV_ERR_NOT_CONVERGED, "CG breakdown: p^dagger A p <= 0 or not finite");
-      const double alpha = rr[r] / pq.x;
-      launch_cg_update_xr(I.pv, static_cast<char*>(e) + r * v1, I.cr.c() + r * v1, I.cp.c() + r * v1,
-                          I.cq.c() + r * v1, alpha, V, 1, c->d_partial.as<double2>(), c->st);
-      OV_TRY(launched(c));
-      double2 rn;
-      OV_TRY(read_reduced(c, c->d_partial.as<double2>(), 1, &rn));
-      const double beta = rn.x / rr[r];
-      rr[r] = rn.x;
-      if (!std::isfinite(rn.x)) return fail(c, OV_ERR_NOT_CONVERGED, "CG residual not finite");
-      if (std::sqrt(rr[r]) <= tol * std::sqrt(rr0[r])) {
-        done[r] = 1;
-        continue;
-      }
-      launch_cg_update_p(I.pv, I.cp.c() + r * v1, I.cr.c() + r * v1, beta, V, 1, c->st);
-      OV_TRY(launched(c));
-    }
-  }
-  *iters = it;
-  for (int r = 0; r < nrhs; ++r)
-    if (!done[r]) return OV_ERR_NOT_CONVERGED;  // caller decides; no message overwrite
-  return OV_OK;
-}
-
-ov_status check_dtype(ov_ctx* c, int nrhs, ov_dtype dt) {
-  if (nrhs < 1) return fail(c, OV_ERR_INVALID, "nrhs must be >= 1");
-  if (nrhs > 65535) return fail(c, OV_ERR_INVALID, "nrhs must be <= 65535 (one stencil grid slot each)");
-  if (dt != OV_C128 && dt != OV_C64) return fail(c, OV_ERR_INVALID, "dtype must be OV_C128 or OV_C64");
-  return OV_OK;
-}
-
-ov_status pack_input(ov_ctx* c, Inst& I, const void* in, int nrhs, ov_dtype dt, void* dst) {
-  const void* din;
-  OV_TRY(stage_in(c, c->stage_in, in, iface_bytes(c->g, nrhs, dt), &din));
-  launch_pack_spinor(I.pv, dt == OV_C128 ? IF_C128 : IF_C64, c->g, din, dst, nrhs, 1.0, 0, c->st);
-  return launched(c);
-}
-
-ov_status unpack_output(ov_ctx* c, Inst& I, const void* src, void* out, int nrhs, ov_dtype dt) {
-  void* dout;
-  bool staged;
-  const size_t bytes = iface_bytes(c->g, nrhs, dt);
-  OV_TRY(stage_out(c, out, bytes, &dout, &staged));
-  launch_unpack_spinor(I.pv, dt == OV_C128 ? IF_C128 : IF_C64, c->g, src, dout, nrhs, 1.0, c->st);
-  OV_TRY(launched(c));
-  return finish_out(c, out, bytes, staged);
-}
-
-// Times one stencil variant on nrhs right-hand sides: a K step and a
-// recurrence step (three extra vector reads), after one warm-up pair.
-ov_status time_variant(ov_ctx* c, Inst& I, const DslashCfg& cfg, const void* links, int nrhs, DevBuf* buf,
-                       cudaEvent_t e0, cudaEvent_t e1, float* ms) {
-  EpiArgs ek;
-  ek.m_w = c->m_w;
-  EpiArgs er = ek;
-  er.v[0] = buf[2].p;
-  er.w[0] = 0.5;
-  er.v[1] = buf[3].p;
-  er.w[1] = -1.0;
-  er.v[2] = buf[0].p;
-  er.w[2] = 0.25;
-  for (int rep = 0; rep < 2; ++rep) {
-    if (rep == 1) OV_CK(cudaEventRecord(e0, c->st));
-    for (int k = 0; k < (nrhs > 4 ? 1 : 3); ++k) {
-      if (!launch_dslash(I.p, I.p, cfg, c->g, links, buf[0].p, buf[1].p, ek, nrhs, c->st) ||
-          !launch_dslash(I.p, I.p, cfg, c->g, links, buf[1].p, buf[3].p, er, nrhs, c->st))
-        return fail(c, OV_ERR_CUDA, "stencil variant not compiled");
-    }
-    OV_TRY(launched(c, 2));
-  }
-  OV_CK(cudaEventRecord(e1, c->st));
-  OV_CK(cudaEventSynchronize(e1));
-  OV_CK(cudaEventElapsedTime(ms, e0, e1));
-  return OV_OK;
-}
-
-// (minb, rt) pairs compiled for the stencil (see dslash_kernel.cuh).
-const int kVariants[][2] = {{2, 1}, {3, 1}, {4, 1}, {2, 2}, {3, 2}, {1, 3}, {2, 3}, {1, 4}, {2, 4}, {1, 6}};
-
-// The environment variable OV_STENCIL="tpb,minb,lrec[,rt]" (e.g. "192,3,12")
-// skips the timing and pins one variant (used for reproducible profiles);
-// OV_STENCIL="slab" pins the slab kernel where it applies (16-bit storage,
-// Lx Ly a multiple of 32 up to 640), the default gather variant elsewhere.
-bool pinned_cfg(DslashCfg* cfg, bool* bad) {
-  *bad = false;
-  const char* env = std::getenv("OV_STENCIL");
-  if (!env) return false;
-  if (std::strcmp(env, "slab") == 0) {
-    *cfg = DslashCfg{};
-    cfg->slab = 1;  // resolved by the caller
-    return true;
-  }
-  int tpb = 0, minb = 0, lrec = 0, rt = 1;
-  const int n = std::sscanf(env, "%d,%d,%d,%d", &tpb, &minb, &lrec, &rt);
-  bool ok = n >= 3 && tpb >= 32 && tpb <= 256 && tpb % 32 == 0 && (lrec == 12 || lrec == 18);
-  bool listed = false;
-  for (const auto& v : kVariants) listed = listed || (v[0] == minb && v[1] == rt);
-  if (!ok || !listed) {
-    *bad = true;
-    return false;
-  }
-  *cfg = DslashCfg{tpb, minb, lrec, rt};
-  return true;
-}
-
-// The slab kernel's configuration for instance I, if it applies: as many
-// persistent CTAs (Lx Ly compute threads + a producer warp) as fit on the SMs.
-bool slab_cfg(ov_ctx* c, const Inst& I, DslashCfg* cfg) {
-  if (!(I.p == OP_F16 || I.p == OP_B16) || c->d_stencil_err == nullptr || !slab_lattice_ok(c->g)) return false;
-  const int per_sm = slab_ctas_per_sm(c->g);
-  if (per_sm <= 0) return false;
-  *cfg = DslashCfg{};
-  cfg->tpb = c->g.L[0] * c->g.L[1] + 32;
-  cfg->minb = 1;
-  cfg->lrec = 12;
-  cfg->slab = c->num_sms * per_sm;
-  cfg->err = c->d_stencil_err;
-  return true;
-}
-
-// Times the one-RHS stencil variants (threads per block, register cap, and
-// for 16-bit links the 12- or 18-real layout) on this lattice and keeps the
-// fastest; the link layout chosen here is kept for every nrhs.
-ov_status autotune(ov_ctx* c, Inst& I, const void* links_dev) {
-  const int64_t V = c->g.V;
-  I.cfg = DslashCfg{};
-  I.cfg_batch.clear();
-  const bool is16 = (I.p == OP_F16 || I.p == OP_B16);
-  DslashCfg pin;
-  bool bad = false;
-  const bool pinned = pinned_cfg(&pin, &bad);
-  if (bad)
-    return fail(c, OV_ERR_INVALID,
-                "OV_STENCIL must be \"slab\" or \"tpb,minb,lrec[,rt]\" naming a compiled variant");
-  DevBuf alt;  // the other 16-bit link layout
-  if (is16 && (!pinned || (pin.slab == 0 && pin.lrec == 18))) {
-    OV_CK(alt.ensure((size_t)link_bytes_per_site_dir(I.p, 18) * 4 * V));
-    launch_pack_links(I.p, 18, c->g, links_dev, alt.p, c->st);
-    OV_TRY(launched(c));
-  }
-  DslashCfg best_cfg;
-  if (pinned && pin.slab) {
-    DslashCfg sc;
-    if (slab_cfg(c, I, &sc)) best_cfg = sc;
-  } else if (pinned) {
-    best_cfg = DslashCfg{pin.tpb, pin.minb, is16 ? pin.lrec : 12, 1};
-    if (I.p == OP_F64 && pin.rt != 1) best_cfg.rt = 1;
-  } else if (V >= 4096) {
-    DevBuf buf[4];
-    for (DevBuf& b : buf) {
-      OV_CK(b.ensure(I.pbytes(V)));
-      OV_CK(cudaMemsetAsync(b.p, 0, I.pbytes(V), c->st));
-    }
-    cudaEvent_t e0, e1;
-    OV_CK(cudaEventCreate(&e0));
-    OV_CK(cudaEventCreate(&e1));
-    struct Cand {
-      float ms;
-      DslashCfg cfg;
-      const void* links;
-    };
-    std::vector<Cand> cands;
-    for (int lrec : {12, 18}) {
-      if (!is16 && lrec == 18) continue;
-      const void* links = (lrec == 18 && is16) ? alt.p : I.links.p;
-      for (int tpb : {64, 96, 128, 192, 256})
-        for (const auto& v : kVariants) {
-          if (v[1] != 1) continue;
-          DslashCfg cfg{tpb, v[0], is16 ? lrec : 12, 1};
-          float ms = 0.f;
-          OV_TRY(time_variant(c, I, cfg, links, 1, buf, e0, e1, &ms));
-          cands.push_back({ms, cfg, links});
-        }
-    }
-    DslashCfg sc;
-    if (slab_cfg(c, I, &sc)) {
-      float ms = 0.f;
-      OV_TRY(time_variant(c, I, sc, I.links.p, 1, buf, e0, e1, &ms));
-      cands.push_back({ms, sc, I.links.p});
-    }
-    // the leaders are often within a few percent: time the best three again,
-    // interleaved, and keep each one's fastest run
-    std::sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) { return x.ms < y.ms; });
-    const size_t top = std::min<size_t>(3, cands.size());
-    for (int rep = 0; rep < 3; ++rep)
-      for (size_t k = 0; k < top; ++k) {
-        float ms = 0.f;
-        OV_TRY(time_variant(c, I, cands[k].cfg, cands[k].links, 1, buf, e0, e1, &ms));
-        cands[k].ms = std::min(cands[k].ms, ms);
-      }
-    size_t win = 0;
-    for (size_t k = 1; k < top; ++k)
-      if (cands[k].ms < cands[win].ms) win = k;
-    if (!cands.empty()) best_cfg = cands[win].cfg;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-  }
-  I.cfg = best_cfg;
-  if (is16 && best_cfg.lrec == 18) std::swap(I.links, alt);
-  OV_CK(cudaStreamSynchronize(c->st));
-  alt.release();
-  return OV_OK;
-}
-
-// Stencil shape for nrhs right-hand sides: tuned on first use (threads per
-// block, register cap, right-hand sides per thread; link layout as tuned at
-// create) and cached per nrhs.
-ov_status batch_cfg(ov_ctx* c, Inst& I, int nrhs, DslashCfg* out) {
-  if (nrhs <= 1) {
-    *out = I.cfg;
-    return OV_OK;
-  }
-  for (const auto& kv : I.cfg_batch)
-    if (kv.first == nrhs) {
-      *out = kv.second;
-      return OV_OK;
-    }
-  DslashCfg best_cfg = I.cfg;
-  DslashCfg pin;
-  bool bad = false;
-  if (pinned_cfg(&pin, &bad)) {
-    if (!pin.slab) {
-      best_cfg = DslashCfg{pin.tpb, pin.minb, I.cfg.lrec, (I.p == OP_F64) ? 1 : pin.rt};
-      if (best_cfg.rt == 1 && best_cfg.minb == 1) best_cfg.minb = 2;
-    }
-  } else if (c->g.V >= 4096) {
-    const int64_t V = c->g.V;
-    DevBuf buf[4];
-    for (DevBuf& b : buf) {
-      OV_CK(b.ensure(I.pbytes(V) * nrhs));
-      OV_CK(cudaMemsetAsync(b.p, 0, I.pbytes(V) * nrhs, c->st));
-    }
-    cudaEvent_t e0, e1;
-    OV_CK(cudaEventCreate(&e0));
-    OV_CK(cudaEventCreate(&e1));
-    float best = 1e30f;
-    for (int tpb : {64, 96, 128, 192, 256})
-      for (const auto& v : kVariants) {
-        if (v[1] > nrhs || (I.p == OP_F64 && v[1] != 1)) continue;
-        DslashCfg cfg{tpb, v[0], I.cfg.lrec, v[1]};
-        float ms = 0.f;
-        OV_TRY(time_variant(c, I, cfg, I.links.p, nrhs, buf, e0, e1, &ms));
-        if (ms < best) {
-          best = ms;
-          best_cfg = cfg;
-        }
-      }
-    DslashCfg sc;
-    if (I.cfg.lrec == 12 && slab_cfg(c, I, &sc)) {
-      float ms = 0.f;
-      OV_TRY(time_variant(c, I, sc, I.links.p, nrhs, buf, e0, e1, &ms));
-      if (ms < best) {
-        best = ms;
-        best_cfg = sc;
-      }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    OV_CK(cudaStreamSynchronize(c->st));
-  }
-  I.cfg_batch.emplace_back(nrhs, best_cfg);
-  *out = best_cfg;
-  return OV_OK;
-}
-
-ov_status init_inst(ov_ctx* c, Inst& I, OpPrec p, const void* links_dev) {
-  I.p = p;
-  I.pv = (p == OP_F64) ? OP_F64 : OP_F32;
-  I.active = true;
-  OV_CK(I.links.ensure((size_t)link_bytes_per_site_dir(p, 12) * 4 * c->g.V));
-  launch_pack_links(p, 12, c->g, links_dev, I.links.p, c->st);
-  OV_TRY(launched(c));
-  OV_TRY(autotune(c, I, links_dev));
-  // 16-bit links fit in L2: mark them persisting for the stencil launches
-  // (a per-process limit, released in ov_destroy).  OV_L2PIN=0 disables.
-  const char* pin = std::getenv("OV_L2PIN");
-  if ((p == OP_F16 || p == OP_B16) && !(pin && std::atoi(pin) == 0)) {
-    const size_t bytes = (size_t)link_bytes_per_site_dir(p, I.cfg.lrec) * 4 * c->g.V;
-    int dev = 0, max_persist = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev) == cudaSuccess &&
-        (size_t)max_persist >= bytes && bytes >= (size_t(1) << 20)) {
-      OV_CK(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, bytes));
-      l2_window().base = I.links.p;
-      l2_window().bytes = bytes;
-      c->l2_pinned = true;
-    }
-  }
-  return OV_OK;
-}
-
 }  // namespace ov
 
 // ===========================================================================
@@ -887,140 +220,6 @@ ov_status ov_overlap(ov_ctx* c, double mu, int dagger, const void* in, void* out
   return unpack_output(c, I, I.xout.p, out, nrhs, dt);
 }
 
-ov_status ov_set_solver_params(ov_ctx* c, double inner_tol, int max_outer) {
-  if (!c) return OV_ERR_INVALID;
-  if (!(inner_tol > 0.0 && inner_tol < 1.0) || max_outer < 1)
-    return fail(c, OV_ERR_INVALID, "need 0 < inner_tol < 1 and max_outer >= 1");
-  c->inner_tol = inner_tol;
-  c->max_outer = max_outer;
-  return OV_OK;
-}
-
-}  // extern "C"
-
-namespace ov {
-
-// CG on D^dagger D x = D^dagger b (chirality 0) or on the chiral-sector
-// operator A x = P b (chirality +-1), FP64 defect correction around the
-// inner solver of the context's precision.
-ov_status solve_core(ov_ctx* c, double mu, int chirality, double tol, int maxit, const void* b, void* x, int nrhs,
-                     ov_dtype dt, int* iters, double* true_rel_resid) {
-  if (!c) return OV_ERR_INVALID;
-  if (!b || !x) return fail(c, OV_ERR_INVALID, "null vector");
-  if (!std::isfinite(mu) || !(tol > 0.0) || maxit < 1)
-    return fail(c, OV_ERR_INVALID, "need finite mu, tol > 0, maxit >= 1");
-  OV_TRY(check_dtype(c, nrhs, dt));
-  if (!c->configured) return fail(c, OV_ERR_STATE, "sign(K) not configured: call ov_sign_config first");
-  c->stats.inner_iterations = 0;
-  c->stats.outer_iterations = 0;
-  Inst& H = c->hi;
-  // inner solver: FP64 itself, or the context-precision operator
-  Inst& I = (c->prec == OV_FP64) ? c->hi : c->lo;
-  const int64_t V = c->g.V;
-  const size_t v1 = H.vbytes(V), vb = v1 * nrhs;
-  const size_t iv1 = I.vbytes(V);
-  OV_TRY(ensure_work(c, H, nrhs));
-  OV_TRY(ensure_work(c, I, nrhs));
-  OV_CK(c->o_x.ensure(vb));
-  OV_CK(c->o_r.ensure(vb));
-  OV_CK(c->o_rhs.ensure(vb));
-  OV_CK(c->o_q.ensure(vb));
-  OV_CK(I.cx.ensure(iv1 * nrhs));
-  // rhs = D^dagger b with the FP64 operator, or P b (the FP64 layout keeps
-  // spinor component 3 spin + colour in chunk k: spins 2, 3 are chunks 6..11)
-  OV_TRY(pack_input(c, H, b, nrhs, dt, H.xin.p));
-  if (chirality == 0) {
-    OV_TRY(sign_core(c, H, H.xin.p, c->o_rhs.p, nrhs, K_OVL_DAG, mu, 1.0));
-  } else {
-    OV_CK(cudaMemcpyAsync(c->o_rhs.p, H.xin.p, vb, cudaMemcpyDeviceToDevice, c->st));
-    const size_t half = v1 / 2;
-    for (int r = 0; r < nrhs; ++r)
-      OV_CK(cudaMemsetAsync(c->o_rhs.c() + r * v1 + (chirality > 0 ? half : 0), 0, half, c->st));
-  }
-  std::vector<double> rhs_n(nrhs), res(nrhs), rn(nrhs);
-  for (int r = 0; r < nrhs; ++r) {
-    OV_TRY(norm2(c, OP_F64, c->o_rhs.c() + r * v1, V, &rhs_n[r]));
-    rhs_n[r] = std::sqrt(rhs_n[r]);
-    res[r] = rhs_n[r] > 0 ? 1.0 : 0.0;
-    rn[r] = rhs_n[r];
-  }
-  OV_CK(cudaMemsetAsync(c->o_x.p, 0, vb, c->st));
-  OV_CK(cudaMemcpyAsync(c->o_r.p, c->o_rhs.p, vb, cudaMemcpyDeviceToDevice, c->st));
-
-  // Defect correction: r = rhs - A x (FP64), solve A e = r / |r| with inner CG,
-  // x += |r| e, recompute r.  With an FP64 inner solver the first pass usually
-  // meets tol already; the loop then only confirms it.
-  const int max_outer = (c->prec == OV_FP64) ? 4 : c->max_outer;
-  int total = 0;
-  bool ok = false;
-  for (int outer = 0; outer < max_outer; ++outer) {
-    double worst = 0;
-    for (double v : res) worst = std::max(worst, v);
-    if (worst <= tol) {
-      ok = true;
-      break;
-    }
-    if (total >= maxit) break;
-    for (int r = 0; r < nrhs; ++r) {
-      launch_convert(OP_F64, I.pv, c->o_r.c() + r * v1, I.xin.c() + r * iv1, V, 1, rn[r] > 0 ? 1.0 / rn[r] : 0.0,
-                     0, c->st);
-      OV_TRY(launched(c));
-    }
-    double inner = 0.5 * tol / worst;
-    if (c->prec != OV_FP64) inner = std::max(inner, c->inner_tol);
-    inner = std::min(inner, 0.5);
-    int it = 0;
-    ov_status s = cg_inner(c, I, I.xin.p, I.cx.p, nrhs, mu, inner, maxit - total, &it, chirality);
-    total += it;
-    if (s != OV_OK && s != OV_ERR_NOT_CONVERGED) return s;
-    for (int r = 0; r < nrhs; ++r) {
-      launch_convert(I.pv, OP_F64, I.cx.c() + r * iv1, c->o_x.c() + r * v1, V, 1, rn[r], 1, c->st);
-      OV_TRY(launched(c));
-    }
-    c->stats.outer_iterations++;
-    // true residual with the FP64 operator
-    OV_TRY(op_apply(c, H, c->o_x.p, c->o_q.p, nrhs, mu, 1.0, chirality));
-    launch_axpby(OP_F64, 1.0, c->o_rhs.p, -1.0, c->o_q.p, c->o_r.p, V, nrhs, c->st);
-    OV_TRY(launched(c));
-    for (int r = 0; r < nrhs; ++r) {
-      double n2;
-      OV_TRY(norm2(c, OP_F64, c->o_r.c() + r * v1, V, &n2));
-      rn[r] = std::sqrt(n2);
-      res[r] = rhs_n[r] > 0 ? rn[r] / rhs_n[r] : 0.0;
-    }
-  }
-  if (!ok) {
-    double worst = 0;
-    for (double v : res) worst = std::max(worst, v);
-    ok = worst <= tol;
-  }
-  c->stats.inner_iterations = total;
-  OV_TRY(unpack_output(c, H, c->o_x.p, x, nrhs, dt));
-  if (iters) *iters = total;
-  double mx = 0;
-  for (double v : res) mx = std::max(mx, v);
-  if (true_rel_resid) *true_rel_resid = mx;
-  if (!ok) return fail(c, OV_ERR_NOT_CONVERGED, "solver stopped before reaching tol");
-  return OV_OK;
-}
-
-}  // namespace ov
-
-extern "C" {
-
-ov_status ov_solve(ov_ctx* c, double mu, double tol, int maxit, const void* b, void* x, int nrhs, ov_dtype dt,
-                   int* iters, double* true_rel_resid) {
-  return solve_core(c, mu, 0, tol, maxit, b, x, nrhs, dt, iters, true_rel_resid);
-}
-
-ov_status ov_solve_chiral(ov_ctx* c, double mu, int chirality, double tol, int maxit, const void* b, void* x,
-                          int nrhs, ov_dtype dt, int* iters, double* true_rel_resid) {
-  if (!c) return OV_ERR_INVALID;
-  if (chirality != 1 && chirality != -1) return fail(c, OV_ERR_INVALID, "chirality must be +1 or -1");
-  if (!(std::fabs(mu) < 1.0)) return fail(c, OV_ERR_INVALID, "need |mu| < 1 (positive definite sector operator)");
-  return solve_core(c, mu, chirality, tol, maxit, b, x, nrhs, dt, iters, true_rel_resid);
-}
-
 ov_status ov_get_stats(const ov_ctx* c, ov_stats* out) {
   if (!c || !out) return OV_ERR_INVALID;
   *out = c->stats;
@@ -1054,3 +253,4 @@ const char* ov_last_error(const ov_ctx* c) {
 }
 
 }  // extern "C"
+

@@ -1,6 +1,7 @@
 // Context of the C ABI and the host-side helpers shared by the drivers
-// (api.cu: operators and solver; eigs_host.cu: eigensolver; grad_host.cu:
-// adjoint).  Not part of the public interface.
+// (api.cu: entry points; sign.cu: sign(K) and the overlap operators; solve.cu:
+// solvers; tune.cu: stencil shapes; ctx.cu: these helpers; eigs_host.cu:
+// eigensolver; grad_host.cu: adjoint).  Not part of the public interface.
 #pragma once
 #include <cmath>
 #include <string>
@@ -127,6 +128,11 @@ ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kin
 ov_status normal_apply(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, double mu, double scale);
 // D^dagger D (chirality 0) or the chiral-sector operator (chirality +-1)
 ov_status op_apply(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, double mu, double scale, int chirality);
+// operator instance in storage p: links packed from the complex128 interface
+// layout, stencil shape tuned, 16-bit links marked persisting in L2 (tune.cu)
+ov_status init_inst(ov_ctx* c, Inst& I, OpPrec p, const void* links_dev);
+// stencil shape for nrhs right-hand sides, tuned on first use (tune.cu)
+ov_status batch_cfg(ov_ctx* c, Inst& I, int nrhs, DslashCfg* out);
 
 }  // namespace ov
 
