@@ -178,8 +178,11 @@ ov_status ov_set_solver_params(ov_ctx* ctx, double inner_tol, int max_outer);
  * with K, in FP64 arithmetic for all inner products.  evals: host, n_ev
  * doubles, ascending |lambda|; evecs: complex128 [n_ev][V][4][3] (host or
  * device).  tol: relative eigen-residual ||K phi - lambda phi|| <= tol * lambda_max.
- * lambda_max_out (may be NULL): an upper bound of |lambda| of K.
- * Errors: OV_ERR_INVALID, OV_ERR_NOT_CONVERGED (best pairs returned). */
+ * lambda_max_out (may be NULL): an upper bound of |lambda| of K.  max_iter
+ * counts filter + Rayleigh-Ritz steps (filter degree 32 on K^2; the
+ * environment variable OV_EIGS_DEGREE overrides it, 4 .. 256).
+ * Errors: OV_ERR_INVALID, OV_ERR_NOT_CONVERGED (best pairs returned; also when
+ * the filtered block stops being finite, with no pairs written). */
 ov_status ov_eigs(ov_ctx* ctx, int n_ev, double tol, int max_iter, double* evals, void* evecs,
                   double* lambda_max_out);
 
