@@ -270,43 +270,6 @@ __device__ __forceinline__ void load_link<F32, float>(const void* p, int mu, int
   }
   reconstruct_row2(u);
 }
-template <class T>
-__device__ __forceinline__ void load_link16(const void* p, int mu, int s, int V, SU3<float>& u) {
-  const uint2* q = static_cast<const uint2*>(p) + (int64_t)mu * 3 * V;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    uint2 v = __ldg(q + c * V + s);
-    float2 a = unpack2<T>(v.x), b = unpack2<T>(v.y);
-    u.u[2 * c] = {a.x, a.y};
-    u.u[2 * c + 1] = {b.x, b.y};
-  }
-  reconstruct_row2(u);
-}
-// 16-bit links with all 9 entries (no reconstruction): 5 uint2 chunks per
-// direction at [(mu*5 + c)*V + s], the second half of chunk 4 unused.
-template <class T>
-__device__ __forceinline__ void load_link16_full(const void* p, int mu, int s, int V, SU3<float>& u) {
-  const uint2* q = static_cast<const uint2*>(p) + (int64_t)mu * 5 * V;
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    uint2 v = __ldg(q + c * V + s);
-    float2 a = unpack2<T>(v.x), b = unpack2<T>(v.y);
-    u.u[2 * c] = {a.x, a.y};
-    u.u[2 * c + 1] = {b.x, b.y};
-  }
-  uint2 v = __ldg(q + 4 * V + s);
-  float2 a = unpack2<T>(v.x);
-  u.u[8] = {a.x, a.y};
-}
-
-template <>
-__device__ __forceinline__ void load_link<F16, float>(const void* p, int mu, int s, int V, SU3<float>& u) {
-  load_link16<F16>(p, mu, s, V, u);
-}
-template <>
-__device__ __forceinline__ void load_link<B16, float>(const void* p, int mu, int s, int V, SU3<float>& u) {
-  load_link16<B16>(p, mu, s, V, u);
-}
 
 // ---------------------------------------------------------------------------
 // lattice geometry

@@ -264,7 +264,9 @@ __device__ __forceinline__ void reconstruct16(uint32_t (&uw)[9]) {
 }
 
 // The 9 packed words of U_mu(s) for 16-bit links: 12 stored reals (row 2
-// rebuilt by reconstruct16) or all 18 (layout of load_link16_full).
+// rebuilt by reconstruct16) or all 18: 5 uint2 chunks per direction at
+// [(mu * 5 + c) V + s], chunk c holding entries 2c and 2c + 1 (the second half
+// of chunk 4 unused).
 template <class T, int LREC>
 __device__ __forceinline__ void load_link_words16(const void* p, int mu, int s, int V, uint32_t (&uw)[9]) {
   const uint2* q = static_cast<const uint2*>(p) + (int64_t)mu * (LREC == 18 ? 5 : 3) * V;
@@ -398,14 +400,5 @@ __device__ __forceinline__ void load_words16(const void* p, int s, int V, uint32
   }
 }
 
-// (1 -/+ gamma_mu) psi as a full spinor
-template <int MU, int SIGN, class R>
-__device__ __forceinline__ void project_full(const Spinor<R>& p, Spinor<R>& out) {
-  Half<R> h;
-  project<MU, SIGN>(p, h);
-#pragma unroll
-  for (int k = 0; k < 12; ++k) out.c[k] = {R(0), R(0)};
-  expand_add<MU, SIGN>(out, h);
-}
 
 }  // namespace ov
