@@ -439,6 +439,8 @@ def extras(args, ctx, links_d, a, b, evals, evecs, psi, vol):
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             st = ov_get_stats(c.handle)
+        if prec == args.prec:
+            x_cg = x
         solves[prec] = {"seconds": dt, "iterations": it, "outer": st["outer_iterations"], "true_rel_resid": r,
                         "mu": MU}
     if "fp64" not in solves:
@@ -487,10 +489,53 @@ def extras(args, ctx, links_d, a, b, evals, evecs, psi, vol):
                             "sign_applies": st["sign_applies"], "true_rel_resid": r}
     chiral["speedup"] = chiral["normal_equations"]["seconds"] / chiral["chiral_sector"]["seconds"]
     solves["chiral_point_source"] = chiral
+    solves["gmresr"] = gmresr_timing(links_d, a, b, evals, evecs, psi, args.prec, solves[args.prec]["seconds"],
+                                     x_cg=x_cg)
     res["solve_1e-10"] = solves
     res["solve_16x16x16x32_fp32"] = solve_16_timing()
     res["gradient"] = gradient_timing()
     return res
+
+
+def gmresr_timing(links_d, a, b, evals, evecs, psi, prec, cg_seconds=None, settings=((0, 0.1),), x_cg=None):
+    """D[mu] x = psi to 1e-10 (||psi - D x|| / ||psi||, FP64 operator) by
+    GMRESR: GCR on D in the storage precision, inner SUMR with a relaxed
+    (lower-order) sign, FP64 defect correction.  settings: (inner order,
+    inner tolerance) pairs; order 0 = automatic (sign error <= 1e-2).  x_cg:
+    the CG (normal equations) solution of the same system, whose
+    ||psi - D x|| / ||psi|| and distance to the GMRESR solution are reported
+    (the CG stops on the normal-equation residual instead)."""
+    import torch
+    from paper_1510_06897_gb300.binding import (Ctx, ov_get_stats, ov_overlap, ov_reset_stats,
+                                                ov_set_gmresr_params, ov_solve_gmresr)
+    out = {}
+    if x_cg is not None:
+        with Ctx(DIMS, links_d, "fp64") as c64:
+            c64.sign_config(ORDER, a, b, evals, evecs)
+            dx = torch.empty_like(psi)
+            ov_overlap(c64.handle, MU, 0, x_cg, dx, 1)
+            out["cg_true_rel_resid_D"] = (torch.linalg.vector_norm(psi - dx) / torch.linalg.vector_norm(psi)).item()
+    with Ctx(DIMS, links_d, prec) as c:
+        c.sign_config(ORDER, a, b, evals, evecs)
+        x = torch.empty_like(psi)
+        for order_in, tol_in in settings:
+            ov_set_gmresr_params(c.handle, order_in, tol_in, 1000, 12)
+            ov_reset_stats(c.handle)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it, r = ov_solve_gmresr(c.handle, MU, 1e-10, 100000, psi, x, 1, allow_not_converged=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            st = ov_get_stats(c.handle)
+            out[f"inner_order_{order_in or 'auto'}_tol_{tol_in}"] = {
+                "precision": prec, "seconds": dt, "sumr_iterations": it, "relaxed_order": st["gmresr_order"],
+                "gcr_steps": st["gcr_iterations"], "fp64_passes": st["outer_iterations"],
+                "sign_applies": st["sign_applies"], "dslash_launches": st["dslash_launches"],
+                "true_rel_resid_D": r, "mu": MU,
+                "speedup_vs_cg_normal_equations": (cg_seconds / dt) if cg_seconds else None,
+                "rel_diff_to_cg_solution": ((torch.linalg.vector_norm(x - x_cg) / torch.linalg.vector_norm(x_cg)).item()
+                                            if x_cg is not None else None)}
+    return out
 
 
 def solve_16_timing():

@@ -78,7 +78,7 @@ typedef struct {
   long long kernel_launches;   /* all kernels launched by this context */
   long long dslash_launches;   /* stencil kernels (one K or D_W application each, all RHS) */
   long long sign_applies;      /* sign(K) applications (per RHS) */
-  long long inner_iterations;  /* CG iterations in the context's precision (last ov_solve) */
+  long long inner_iterations;  /* CG (SUMR) iterations in the context's precision (last solve) */
   long long outer_iterations;  /* FP64 defect-correction steps (last ov_solve) */
   long long dslash_timed;      /* stencil launches timed while profiling was on */
   double dslash_ms;            /* their summed device time (CUDA events on the context stream) */
@@ -88,6 +88,9 @@ typedef struct {
   int tc_gemm_launches;        /* deflation projections run on the tensor cores (several RHS, FP32 vectors) */
   int stencil_slab;            /* > 0: the tuned stencil is the slab kernel on this many persistent CTAs
                                   (stencil_tpb = Lx*Ly + 32 threads each); 0: the gather kernel */
+  long long gcr_iterations;    /* GCR steps of the last ov_solve_gmresr (inner_iterations: its SUMR
+                                  iterations) */
+  int gmresr_order;            /* Chebyshev order of the relaxed sign in that solve */
 } ov_stats;
 
 /* Creates a context for one lattice and gauge field (Eq. 2 links).  Copies and
@@ -169,8 +172,52 @@ ov_status ov_solve_chiral(ov_ctx* ctx, double mu, int chirality, double tol, int
 
 /* Inner-solver controls for the mixed-precision defect correction: relative
  * tolerance of each inner solve (default 1e-5) and the maximum number of FP64
- * outer steps (default 30). */
+ * outer steps (default 30).  They apply to ov_solve, ov_solve_chiral and
+ * ov_solve_gmresr. */
 ov_status ov_set_solver_params(ov_ctx* ctx, double inner_tol, int max_outer);
+
+/* Shifted-unitary minimal residual solve of D[mu] x = b (the SUMR named in
+ * Sec. 2 as the inner solver of GMRESR(eigSUMR)).  Eq. 1 reads
+ * D[mu] = (1-mu)/2 (U - zeta) with U = gamma5 sign(K) and
+ * zeta = -(1+mu)/(1-mu); the iterate after k products with U is the minimal
+ * residual one over the Krylov space of U when U is unitary, built by the
+ * Szego recursion of U's orthonormal polynomials (short recurrences, six
+ * vectors, one sign(K) application per iteration; the new Krylov pair is
+ * normalised by its computed norms, which keeps the recursion stable for the
+ * polynomial sign).  Runs in the context's precision with the configured
+ * sign (no defect correction) until the estimate 1/sqrt(s_k) of
+ * ||b - D x|| / ||b|| is <= tol for every RHS, or maxit iterations (tol = 0:
+ * exactly maxit).  iters (may be NULL): iterations; est_rel_resid (may be
+ * NULL): the largest final estimate (exact for unitary U; with the
+ * polynomial sign it tracks the true residual).  Errors: OV_ERR_INVALID
+ * (|mu| >= 1, tol < 0, maxit < 0, as ov_solve), OV_ERR_STATE,
+ * OV_ERR_NOT_CONVERGED if the recursion produced a non-finite value. */
+ov_status ov_sumr(ov_ctx* ctx, double mu, double tol, int maxit, const void* b, void* x, int nrhs, ov_dtype dtype,
+                  int* iters, double* est_rel_resid);
+
+/* GMRESR for D[mu] x = b (Sec. 2: recursive GMRES preconditioned by a
+ * low-accuracy SUMR solve with a relaxed sign function).  Three levels:
+ * FP64 defect correction on D[mu] (as ov_solve, on D itself); inside it GCR
+ * on D[mu] in the context precision with the configured sign, its
+ * directions kept and orthogonalised (up to max_dirs, then restarted); each
+ * direction an ov_sumr-type solve with a LOWER-order Chebyshev polynomial on
+ * the same interval (the relaxed sign; see ov_set_gmresr_params).  Stops when
+ * ||b - D x|| / ||b|| <= tol for every RHS, recomputed with the FP64
+ * operator.  iters (may be NULL): total SUMR iterations; ov_stats counts the
+ * GCR steps (gcr_iterations) and FP64 passes (outer_iterations).
+ * true_rel_resid, errors: as ov_solve; OV_ERR_INVALID for |mu| >= 1. */
+ov_status ov_solve_gmresr(ov_ctx* ctx, double mu, double tol, int maxit, const void* b, void* x, int nrhs,
+                          ov_dtype dtype, int* iters, double* true_rel_resid);
+
+/* GMRESR controls.  inner_order: Chebyshev order of the relaxed sign of the
+ * inner SUMR solves (0, the default: the smallest order whose sign error
+ * max |sqrt(y) f_N(y) - 1| on [lo^2, hi^2] is <= 1e-2; never above the
+ * configured order).  inner_tol: estimate at which an inner solve stops
+ * (default 0.1).  inner_maxit: iterations per inner solve (default 1000).
+ * max_dirs: GCR directions kept before a restart (1..64, default 12; each
+ * costs two vectors per RHS in the context's vector precision).
+ * OV_ERR_INVALID otherwise. */
+ov_status ov_set_gmresr_params(ov_ctx* ctx, int inner_order, double inner_tol, int inner_maxit, int max_dirs);
 
 /* Computes the n_ev eigenpairs of K of smallest |lambda| (the input of the
  * deflation in Eq. 3; Sec. 2 uses a polynomial-preconditioned Lanczos), by

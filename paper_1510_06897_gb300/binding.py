@@ -45,7 +45,9 @@ class ov_stats(ctypes.Structure):
                 ("stencil_minb", ctypes.c_int),
                 ("stencil_lrec", ctypes.c_int),
                 ("tc_gemm_launches", ctypes.c_int),
-                ("stencil_slab", ctypes.c_int)]
+                ("stencil_slab", ctypes.c_int),
+                ("gcr_iterations", ctypes.c_longlong),
+                ("gmresr_order", ctypes.c_int)]
 
 
 _LIB = None
@@ -65,6 +67,9 @@ _SIGNATURES = {
     "ov_solve": [_vp, _d, _d, _i, _vp, _vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)],
     "ov_solve_chiral": [_vp, _d, _i, _d, _i, _vp, _vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)],
     "ov_set_solver_params": [_vp, _d, _i],
+    "ov_sumr": [_vp, _d, _d, _i, _vp, _vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)],
+    "ov_solve_gmresr": [_vp, _d, _d, _i, _vp, _vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)],
+    "ov_set_gmresr_params": [_vp, _i, _d, _i, _i],
     "ov_eigs": [_vp, _i, _d, _i, ctypes.POINTER(_d), _vp, ctypes.POINTER(_d)],
     "ov_sign_poly_grad": [_vp, _i, _d, _d, _vp, _vp, _i],
     "ov_get_stats": [_vp, ctypes.POINTER(ov_stats)],
@@ -200,6 +205,31 @@ def ov_solve_chiral(ctx, mu, chirality, tol, maxit, b, x, nrhs, allow_not_conver
     return it.value, res.value
 
 
+def ov_sumr(ctx, mu, tol, maxit, b, x, nrhs):
+    """SUMR for D[mu] x = b (see overlap.h); returns (iterations, residual estimate)."""
+    it = _i(0)
+    est = _d(0.0)
+    _check(lib().ov_sumr(ctx, float(mu), float(tol), int(maxit), _ptr(b), _ptr(x), int(nrhs), _dtype_code(b),
+                         ctypes.byref(it), ctypes.byref(est)), ctx)
+    return it.value, est.value
+
+
+def ov_solve_gmresr(ctx, mu, tol, maxit, b, x, nrhs, allow_not_converged=False):
+    """GMRESR for D[mu] x = b (see overlap.h); returns (SUMR iterations, true relative residual)."""
+    it = _i(0)
+    res = _d(0.0)
+    st = lib().ov_solve_gmresr(ctx, float(mu), float(tol), int(maxit), _ptr(b), _ptr(x), int(nrhs), _dtype_code(b),
+                               ctypes.byref(it), ctypes.byref(res))
+    if not (allow_not_converged and st == OV_ERR_NOT_CONVERGED):
+        _check(st, ctx)
+    return it.value, res.value
+
+
+def ov_set_gmresr_params(ctx, inner_order=0, inner_tol=0.1, inner_maxit=1000, max_dirs=12):
+    return _check(lib().ov_set_gmresr_params(ctx, int(inner_order), float(inner_tol), int(inner_maxit),
+                                             int(max_dirs)), ctx)
+
+
 def ov_set_solver_params(ctx, inner_tol, max_outer):
     return _check(lib().ov_set_solver_params(ctx, float(inner_tol), int(max_outer)), ctx)
 
@@ -310,6 +340,16 @@ class Ctx:
     def solve_chiral(self, b, mu, chirality, tol=1e-10, maxit=5000):
         x = self._like(b)
         it, res = ov_solve_chiral(self.handle, mu, chirality, tol, maxit, b, x, b.shape[0])
+        return x, it, res
+
+    def sumr(self, b, mu, tol=0.0, maxit=100):
+        x = self._like(b)
+        it, est = ov_sumr(self.handle, mu, tol, maxit, b, x, b.shape[0])
+        return x, it, est
+
+    def solve_gmresr(self, b, mu, tol=1e-10, maxit=20000):
+        x = self._like(b)
+        it, res = ov_solve_gmresr(self.handle, mu, tol, maxit, b, x, b.shape[0])
         return x, it, res
 
     def stats(self):

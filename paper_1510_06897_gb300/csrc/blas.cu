@@ -575,6 +575,91 @@ void launch_cg_update_p(OpPrec p, void* pv, const void* r, double beta, int64_t 
   launch_axpby(p, 1.0, r, beta, pv, pv, V, nrhs, st);
 }
 
+// y = y + a x, complex a (GCR updates and orthogonalisation)
+template <class T>
+__global__ void k_caxpy(double2 a, const typename Unit<T>::U* __restrict__ x, typename Unit<T>::U* __restrict__ y,
+                        int64_t n) {
+  using R = typename Arith<T, T>::R;
+  constexpr int m = Unit<T>::n;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const cplx<R> ac = {R(a.x), R(a.y)};
+  cplx<R> xv[m], yv[m];
+  Unit<T>::load(x[i], xv);
+  Unit<T>::load(y[i], yv);
+#pragma unroll
+  for (int k = 0; k < m; ++k) yv[k] = yv[k] + cmul(ac, xv[k]);
+  y[i] = Unit<T>::store(yv);
+}
+
+void launch_caxpy(OpPrec p, double2 a, const void* x, void* y, int64_t V, int nrhs, cudaStream_t st) {
+  OV_DISPATCH1(p, T, {
+    using U = typename Unit<T>::U;
+    const int64_t n = n_units<T>(V, nrhs);
+    k_caxpy<T><<<grid_for(n), kThreads, 0, st>>>(a, static_cast<const U*>(x), static_cast<U*>(y), n);
+  });
+}
+
+// One SUMR step on lazily normalised vectors (see SumrCoef): the deferred
+// X term, the divided-difference pair, the new Krylov pair, and the squared
+// norms of the new (unnormalised) Krylov pair in partial[] (x: V, y: T).
+template <class T>
+__global__ void __launch_bounds__(kReduceThreads) k_sumr_update(typename Unit<T>::U* __restrict__ v,
+                                                                typename Unit<T>::U* __restrict__ vt,
+                                                                const typename Unit<T>::U* __restrict__ w,
+                                                                typename Unit<T>::U* __restrict__ dh,
+                                                                typename Unit<T>::U* __restrict__ dth,
+                                                                typename Unit<T>::U* __restrict__ x, SumrCoef c,
+                                                                int64_t n, double2* __restrict__ partial) {
+  using R = typename Arith<T, T>::R;
+  constexpr int m = Unit<T>::n;
+  __shared__ double2 smem[32];
+  const cplx<R> cx = {R(c.cx.x), R(c.cx.y)}, mt = {R(c.mt.x), R(c.mt.y)}, mc = {R(c.mc.x), R(c.mc.y)},
+                mcv = {R(c.mcv.x), R(c.mcv.y)};
+  const R av = R(c.av), at = R(c.at), zv = R(c.zv);
+  double2 acc = make_double2(0.0, 0.0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    cplx<R> vv[m], tv[m], wv[m], dv[m], dtv[m], xv[m];
+    Unit<T>::load(v[i], vv);
+    Unit<T>::load(vt[i], tv);
+    Unit<T>::load(w[i], wv);
+    Unit<T>::load(dh[i], dv);
+    Unit<T>::load(dth[i], dtv);
+    Unit<T>::load(x[i], xv);
+    R nv = R(0), nt = R(0);
+#pragma unroll
+    for (int k = 0; k < m; ++k) {
+      xv[k] = xv[k] + cmul(cx, dv[k]);
+      const cplx<R> t = av * vv[k] + zv * dv[k];
+      dv[k] = t - cmul(mt, dtv[k]);
+      dtv[k] = at * dtv[k] - cmul(mc, t);
+      vv[k] = av * wv[k] - cmul(mt, tv[k]);
+      tv[k] = at * tv[k] - cmul(mcv, wv[k]);
+      nv += vv[k].re * vv[k].re + vv[k].im * vv[k].im;
+      nt += tv[k].re * tv[k].re + tv[k].im * tv[k].im;
+    }
+    v[i] = Unit<T>::store(vv);
+    vt[i] = Unit<T>::store(tv);
+    dh[i] = Unit<T>::store(dv);
+    dth[i] = Unit<T>::store(dtv);
+    x[i] = Unit<T>::store(xv);
+    acc.x += (double)nv;
+    acc.y += (double)nt;
+  }
+  acc = block_sum(acc, smem);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+void launch_sumr_update(OpPrec p, void* v, void* vt, const void* w, void* dh, void* dth, void* x, const SumrCoef& c,
+                        int64_t V, double2* partial, cudaStream_t st) {
+  OV_DISPATCH1(p, T, {
+    using U = typename Unit<T>::U;
+    k_sumr_update<T><<<kReduceBlocks, kReduceThreads, 0, st>>>(
+        static_cast<U*>(v), static_cast<U*>(vt), static_cast<const U*>(w), static_cast<U*>(dh), static_cast<U*>(dth),
+        static_cast<U*>(x), c, n_units<T>(V, 1), partial);
+  });
+}
+
 // per-site conversion between storages (layouts differ between storages)
 template <class TI, class TO>
 __global__ void k_convert(const char* __restrict__ in, char* out, int64_t V, int64_t in_rb, int64_t out_rb,

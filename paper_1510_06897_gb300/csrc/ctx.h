@@ -44,10 +44,14 @@ struct Inst {
   DevBuf xin, xout, d, tmp;          // pv
   DevBuf perp, t, bA, bB;            // p
   DevBuf cx, cr, cp, cq;             // pv: inner CG
+  DevBuf sv, svt, sw, sdh, sdt, sx;  // pv: SUMR
+  DevBuf gr, grhs, gu, gc;           // pv: GCR residual, inner right-hand side, directions u_i and c_i = D u_i
   size_t vbytes(int64_t V) const { return (size_t)spinor_bytes_per_site(pv) * V; }
   size_t pbytes(int64_t V) const { return (size_t)spinor_bytes_per_site(p) * V; }
   void release() {
-    for (DevBuf* b : {&links, &evecs, &xin, &xout, &d, &tmp, &perp, &t, &bA, &bB, &cx, &cr, &cp, &cq}) b->release();
+    for (DevBuf* b : {&links, &evecs, &xin, &xout, &d, &tmp, &perp, &t, &bA, &bB, &cx, &cr, &cp, &cq, &sv, &svt, &sw,
+                      &sdh, &sdt, &sx, &gr, &grhs, &gu, &gc})
+      b->release();
   }
 };
 
@@ -85,6 +89,14 @@ struct ov_ctx {
   // solver controls
   double inner_tol = 1e-5;
   int max_outer = 30;
+  // GMRESR: inner SUMR order (0: automatic), tolerance, products per inner
+  // solve, GCR directions kept; the relaxed coefficients and what they were made for
+  int gm_order = 0;
+  double gm_tol = 0.1;
+  int gm_maxit = 1000;
+  int gm_dirs = 12;
+  std::vector<double> coef_relaxed;
+  double relaxed_key[4] = {0, 0, 0, 0};
   ov_stats stats{};
   std::string err;
   // stencil profiling (ov_set_profiling): 1 = an event pair around every
@@ -124,7 +136,12 @@ ov_status prof_open(ov_ctx* c);
 ov_status prof_close(ov_ctx* c, int n);
 // out (storage I.p) = stencil epilogue of K applied to `in` (see EpiArgs)
 ov_status k_step(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, const EpiArgs& e);
-ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kind kind, double mu, double scale);
+// cf: Chebyshev coefficients to use instead of the configured ones (a
+// lower-order polynomial on the same interval), or null
+ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kind kind, double mu, double scale,
+                    const std::vector<double>* cf = nullptr);
+// max over [a^2, b^2] of |sqrt(y) f_N(y) - 1| for the coefficients cf (sign.cu)
+double chebyshev_sign_error(const std::vector<double>& cf, double a, double b);
 ov_status normal_apply(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, double mu, double scale);
 // D^dagger D (chirality 0) or the chiral-sector operator (chirality +-1)
 ov_status op_apply(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, double mu, double scale, int chirality);

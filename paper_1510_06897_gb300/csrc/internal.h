@@ -131,6 +131,25 @@ void launch_cg_update_p(OpPrec p, void* pv, const void* r, double beta, int64_t 
 // out = a*x + b*y (out may alias x or y; y may be null => out = a*x)
 void launch_axpby(OpPrec p, double a, const void* x, double b, const void* y, void* out, int64_t V, int nrhs,
                   cudaStream_t st);
+// y = y + a x with complex a
+void launch_caxpy(OpPrec p, double2 a, const void* x, void* y, int64_t V, int nrhs, cudaStream_t st);
+// One step of the shifted-unitary minimal residual recursion (one RHS) on
+// lazily normalised vectors: the stored V, T, Dh, Dth are the true v_j,
+// v~_j, D_j, D~_j times the divisors of the previous step, W = U V.
+//   X += cx Dh;  t = av V + zv Dh;  Dh = t - mt Dth;  Dth = at Dth - mc t;
+//   V = av W - mt T;  T = at T - mcv W;
+// partial[blk] = block sums of (|V|^2, |T|^2) of the new V and T.
+struct SumrCoef {
+  double2 cx;   // conj(phi_j(zeta)) / rho_{j-1}: the deferred term of X
+  double av;    // 1 / rho_{j-1}: v_j = av V, D_j = av Dh
+  double at;    // 1 / rho~_{j-1}: v~_j = at T, D~_j = at Dth
+  double zv;    // zeta av
+  double2 mt;   // m at
+  double2 mc;   // conj(m)
+  double2 mcv;  // conj(m) av
+};
+void launch_sumr_update(OpPrec p, void* v, void* vt, const void* w, void* dh, void* dth, void* x, const SumrCoef& c,
+                        int64_t V, double2* partial, cudaStream_t st);
 // out (storage po) = scale * in (storage pi)            (accumulate = 0)
 // out (storage po) = out + scale * in (storage pi)      (accumulate = 1)
 void launch_convert(OpPrec pi, OpPrec po, const void* in, void* out, int64_t V, int nrhs, double scale,

@@ -42,7 +42,29 @@ ov_status k_step(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, const 
 // sign(K) / D[mu] / D[mu]^dagger on nrhs vectors in I.pv storage.
 // scale: the recurrence runs on scale * (input); results are unscaled in the
 // final epilogue (used to keep 16-bit storage in range).
-ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kind kind, double mu, double scale) {
+// max over [a^2, b^2] of |sqrt(y) f_N(y) - 1|, f_N = c_0/2 + sum_j c_j T_j(z),
+// sampled at 2049 Chebyshev-Lobatto points of z (dense near both ends).
+double chebyshev_sign_error(const std::vector<double>& cf, double a, double b) {
+  const int n = (int)cf.size() - 1, M = 2049;
+  const double pi = 3.14159265358979323846;
+  double worst = 0.0;
+  for (int i = 0; i < M; ++i) {
+    const double z = std::cos(pi * i / (M - 1));
+    const double y = 0.5 * ((b * b - a * a) * z + b * b + a * a);
+    double b1 = 0.0, b2 = 0.0;  // Clenshaw for sum_{j>=1} c_j T_j(z) + c_0/2
+    for (int j = n; j >= 1; --j) {
+      const double b0 = 2.0 * z * b1 - b2 + cf[j];
+      b2 = b1;
+      b1 = b0;
+    }
+    const double f = z * b1 - b2 + 0.5 * cf[0];
+    worst = std::max(worst, std::fabs(std::sqrt(y) * f - 1.0));
+  }
+  return worst;
+}
+
+ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kind kind, double mu, double scale,
+                    const std::vector<double>* cf_override) {
   if (!c->configured) return fail(c, OV_ERR_STATE, "sign(K) not configured: call ov_sign_config first");
   OV_TRY(ensure_work(c, I, nrhs));
   const int64_t V = c->g.V;
@@ -109,8 +131,8 @@ ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kin
   // recurrence algebra in its epilogue.
   const double a2 = c->a * c->a, b2 = c->b * c->b;
   const double alpha = 2.0 / (b2 - a2), beta = -(b2 + a2) / (b2 - a2);
-  const std::vector<double>& cf = c->coef;
-  const int N = c->order;
+  const std::vector<double>& cf = cf_override ? *cf_override : c->coef;
+  const int N = (int)cf.size() - 1;
   void* perp = I.perp.p;
   struct Vec {
     void* p;

@@ -74,6 +74,9 @@ def test_null_context_calls(lib):
     assert lib.ov_sign_apply(None, None, None, 1, 0) == binding.OV_ERR_INVALID
     assert lib.ov_solve(None, 0.1, 1e-10, 10, None, None, 1, 0, None, None) == binding.OV_ERR_INVALID
     assert lib.ov_solve_chiral(None, 0.1, 1, 1e-10, 10, None, None, 1, 0, None, None) == binding.OV_ERR_INVALID
+    assert lib.ov_sumr(None, 0.1, 1e-10, 10, None, None, 1, 0, None, None) == binding.OV_ERR_INVALID
+    assert lib.ov_solve_gmresr(None, 0.1, 1e-10, 10, None, None, 1, 0, None, None) == binding.OV_ERR_INVALID
+    assert lib.ov_set_gmresr_params(None, 0, 0.1, 100, 8) == binding.OV_ERR_INVALID
     assert lib.ov_get_stats(None, None) == binding.OV_ERR_INVALID
 
 
