@@ -18,6 +18,7 @@ can check it against the paper by eye:
   cg         textbook conjugate gradient on D^dagger D
   sumr       shifted-unitary minimal residual (SUMR) for D[mu] and the GMRESR
              (GCR) outer loop around a relaxed inner SUMR (Sec. 2)
+  smear      over-improved stout smearing of the links (Sec. 3 input preparation)
   dense      dense matrices of D_W / K on tiny lattices and the exact
              sign(K) = V sign(Lambda) V^dagger
   force      gradient of chi^dagger P(K) chi with respect to the links
@@ -28,4 +29,4 @@ Parity status of each function is listed in its module docstring; all of
 them are pinned by tests in ``tests/test_oracle_*.py`` against closed forms,
 dense linear algebra, invariants or finite differences.
 """
-from . import wilson, chebyshev, overlap, cg, dense, force, sumr  # noqa: F401
+from . import wilson, chebyshev, overlap, cg, dense, force, sumr, smear  # noqa: F401
