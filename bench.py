@@ -492,6 +492,7 @@ def extras(args, ctx, links_d, a, b, evals, evecs, psi, vol):
     solves["gmresr"] = gmresr_timing(links_d, a, b, evals, evecs, psi, args.prec, solves[args.prec]["seconds"],
                                      x_cg=x_cg)
     res["solve_1e-10"] = solves
+    res["stout_smearing"] = smear_timing(links_d)
     res["solve_16x16x16x32_fp32"] = solve_16_timing()
     res["gradient"] = gradient_timing()
     return res
@@ -536,6 +537,47 @@ def gmresr_timing(links_d, a, b, evals, evecs, psi, prec, cg_seconds=None, setti
                 "rel_diff_to_cg_solution": ((torch.linalg.vector_norm(x - x_cg) / torch.linalg.vector_norm(x_cg)).item()
                                             if x_cg is not None else None)}
     return out
+
+
+def _plaquette(u):
+    """Average (1/3) Re tr of the plaquettes of device links (4, Lt, Lz, Ly, Lx, 3, 3)."""
+    import torch
+    axis = (3, 2, 1, 0)
+    tot = 0.0
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            p = (u[mu] @ torch.roll(u[nu], -1, axis[mu])
+                 @ torch.roll(u[mu], -1, axis[nu]).conj().transpose(-1, -2) @ u[nu].conj().transpose(-1, -2))
+            tot += (p.diagonal(dim1=-2, dim2=-1).sum(-1).real.mean() / 3).item()
+    return tot / 6
+
+
+def smear_timing(links_d):
+    """3 steps of over-improved stout smearing (rho = 0.1, eps = -0.25) of the
+    24^3 x 48 field: time (CUDA events) and the average plaquette before and
+    after each step."""
+    import torch
+    from paper_1510_06897_gb300.binding import ov_stout_smear
+    out = torch.empty_like(links_d)
+    ov_stout_smear(DIMS, links_d, out, 0.1, -0.25, 3)  # warm-up
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    ov_stout_smear(DIMS, links_d, out, 0.1, -0.25, 3)
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    plaq = [_plaquette(links_d)]
+    cur = links_d.clone()
+    for _ in range(3):
+        ov_stout_smear(DIMS, cur, cur, 0.1, -0.25, 1)
+        plaq.append(_plaquette(cur))
+    del cur
+    vol = 1
+    for d in DIMS:
+        vol *= d
+    return {"ms_3_steps": ms, "links_per_s": 3 * 4 * vol / (ms * 1e-3), "plaquette_per_step": plaq,
+            "rho": 0.1, "eps": -0.25, "precision": "fp64"}
 
 
 def solve_16_timing():

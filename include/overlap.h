@@ -275,6 +275,27 @@ ov_status ov_reset_stats(ov_ctx* ctx);
 ov_status ov_wilson_noalloc(const int dims[4], const void* links, const void* in, void* out, int nrhs,
                             ov_dtype dtype, int antiperiodic_t, void* cuda_stream);
 
+/* Over-improved stout smearing of a gauge field (Sec. 3 prepares its
+ * ensembles with 3 steps at rho = 0.1, eps = -0.25: the stout smearing of
+ * Morningstar and Peardon with the over-improved staple of Moran and
+ * Leinweber).  Each step replaces every link at once (from the old field) by
+ *   U' = exp(A) U,  A = 1/2 (Omega - Omega^dagger) - 1/6 tr(Omega - Omega^dagger),
+ *   Omega = rho [ (5 - 2 eps)/3 (6 plaquette staples) - (1 - eps)/12
+ *           (18 rectangle staples: per plane and side the 1x2 rectangle out
+ *           two steps and the two 2x1 rectangles with the link first or
+ *           second on the long side) ] U^dagger,
+ * a staple being the path-ordered product from x to x + mu^ (eps = 1: plain
+ * stout; eps = 0: tree-level Symanzik staple).  No context is needed.
+ * links_in, links_out: device complex128 [4][V][3][3] (the ov_create layout),
+ * may be the same buffer.  steps >= 0 (0 copies).  FP64 throughout; two
+ * temporary link fields are allocated and freed inside the call.  Work runs on
+ * cuda_stream (NULL = legacy default stream) and the call returns when it is
+ * complete.  Errors (text: ov_last_error(NULL)): OV_ERR_INVALID (null or host
+ * pointers, an extent < 2, V > 2^27, steps < 0, non-finite rho or eps),
+ * OV_ERR_NOMEM, OV_ERR_CUDA. */
+ov_status ov_stout_smear(const int dims[4], const void* links_in, void* links_out, double rho, double epsilon,
+                         int steps, void* cuda_stream);
+
 /* Last error message of the context ("" if none); never NULL.  Passing NULL
  * returns the message of the last failed ov_create or ov_wilson_noalloc call
  * on this thread. */

@@ -76,6 +76,7 @@ _SIGNATURES = {
     "ov_reset_stats": [_vp],
     "ov_set_profiling": [_vp, _i],
     "ov_wilson_noalloc": [ctypes.POINTER(_i), _vp, _vp, _vp, _i, _i, _i, _vp],
+    "ov_stout_smear": [ctypes.POINTER(_i), _vp, _vp, _d, _d, _i, _vp],
 }
 
 
@@ -261,6 +262,13 @@ def ov_wilson_noalloc(dims, links, inp, out, nrhs, antiperiodic_t=False, stream=
     cdims = (_i * 4)(*[int(d) for d in dims])
     return _check(lib().ov_wilson_noalloc(cdims, _ptr(links), _ptr(inp), _ptr(out), int(nrhs), _dtype_code(inp),
                                           int(bool(antiperiodic_t)), _stream_ptr(stream)), None)
+
+
+def ov_stout_smear(dims, links_in, links_out, rho=0.1, eps=-0.25, steps=3, stream=None):
+    """Over-improved stout smearing (see overlap.h); links_out may be links_in."""
+    cdims = (_i * 4)(*[int(d) for d in dims])
+    return _check(lib().ov_stout_smear(cdims, _ptr(links_in), _ptr(links_out), float(rho), float(eps), int(steps),
+                                       _stream_ptr(stream)), None)
 
 
 def ov_set_profiling(ctx, on):

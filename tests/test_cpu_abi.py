@@ -77,6 +77,19 @@ def test_null_context_calls(lib):
     assert lib.ov_sumr(None, 0.1, 1e-10, 10, None, None, 1, 0, None, None) == binding.OV_ERR_INVALID
     assert lib.ov_solve_gmresr(None, 0.1, 1e-10, 10, None, None, 1, 0, None, None) == binding.OV_ERR_INVALID
     assert lib.ov_set_gmresr_params(None, 0, 0.1, 100, 8) == binding.OV_ERR_INVALID
+
+
+def test_stout_smear_rejects_bad_arguments_before_device_work(lib):
+    dims = (ctypes.c_int * 4)(4, 4, 4, 4)
+    links = np.zeros((4, 4, 4, 4, 4, 3, 3), dtype=np.complex128)
+    p = links.ctypes.data
+    assert lib.ov_stout_smear(None, p, p, 0.1, -0.25, 3, None) == binding.OV_ERR_INVALID
+    assert lib.ov_stout_smear(dims, None, p, 0.1, -0.25, 3, None) == binding.OV_ERR_INVALID
+    bad = (ctypes.c_int * 4)(4, 1, 4, 4)
+    assert lib.ov_stout_smear(bad, p, p, 0.1, -0.25, 3, None) == binding.OV_ERR_INVALID
+    assert lib.ov_stout_smear(dims, p, p, 0.1, -0.25, -1, None) == binding.OV_ERR_INVALID
+    assert lib.ov_stout_smear(dims, p, p, float("nan"), -0.25, 3, None) == binding.OV_ERR_INVALID
+    assert b"extent" in lib.ov_last_error(None) or b"steps" in lib.ov_last_error(None)
     assert lib.ov_get_stats(None, None) == binding.OV_ERR_INVALID
 
 
