@@ -463,6 +463,8 @@ def extras(args, ctx, links_d, a, b, evals, evecs, psi, vol):
         solves["batched_12_point_sources"] = {
             "precision": args.prec, "seconds": dt, "iterations": it, "outer": st["outer_iterations"],
             "true_rel_resid": r, "fp64_estimate_seconds": 12 * 2 * solves[args.prec]["iterations"] * fp64_apply}
+        solves["batched_12_point_sources_gmresr"] = gmresr_batched_timing(links_d, a, b, evals, evecs, src,
+                                                                          args.prec)
     # chiral point source (spin 0, colour 0 at the origin: chirality +1): D^-1 b
     # from the chiral-sector solve (one sign apply per iteration) + one D^dagger,
     # against the D^dagger D solve of the same source
@@ -537,6 +539,25 @@ def gmresr_timing(links_d, a, b, evals, evecs, psi, prec, cg_seconds=None, setti
                 "rel_diff_to_cg_solution": ((torch.linalg.vector_norm(x - x_cg) / torch.linalg.vector_norm(x_cg)).item()
                                             if x_cg is not None else None)}
     return out
+
+
+def gmresr_batched_timing(links_d, a, b, evals, evecs, src, prec):
+    """D[mu] x = src for all right-hand sides of src in one ov_solve_gmresr
+    call (batched stencil launches), to 1e-10 in ||b - D x|| / ||b||."""
+    import torch
+    from paper_1510_06897_gb300.binding import Ctx, ov_get_stats, ov_solve_gmresr
+    with Ctx(DIMS, links_d, prec) as c:
+        c.sign_config(ORDER, a, b, evals, evecs)
+        x = torch.empty_like(src)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it, r = ov_solve_gmresr(c.handle, MU, 1e-10, 200000, src, x, src.shape[0], allow_not_converged=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st = ov_get_stats(c.handle)
+    return {"precision": prec, "nrhs": int(src.shape[0]), "seconds": dt, "sumr_iterations": it,
+            "relaxed_order": st["gmresr_order"], "gcr_steps": st["gcr_iterations"],
+            "fp64_passes": st["outer_iterations"], "true_rel_resid_D": r}
 
 
 def _plaquette(u):
