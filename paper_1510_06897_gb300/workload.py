@@ -7,7 +7,11 @@ builds the seeded links (exp(i 0.3 H)), takes n_ev orthonormal vectors from a
 single Rayleigh-Ritz pass of ov_eigs (the same amount of deflation work as
 converged eigenvectors; the eigensolver itself is left out of the profile),
 configures sign(K) on [lo, hi] and runs `applies` sign(K) applications (or
-D^dagger D solves with --solve), all through the C ABI.
+D^dagger D solves with --solve, GMRESR solves of D x = b with --gmresr), all
+through the C ABI.  --eigs-tol converges the eigenpairs instead (n_ev + 1 of
+them; the interval then becomes [|lambda_{n_ev+1}|, lambda_max]).
+--profile-range brackets the timed loop with cudaProfilerStart/Stop, so that
+`ncu --profile-from-start off` sees only those launches.
 """
 import argparse
 import sys
@@ -18,7 +22,8 @@ def main(argv=None):
     import torch
 
     from . import inputs
-    from .binding import Ctx, ov_eigs, ov_get_stats, ov_reset_stats, ov_set_profiling, ov_sign_apply, ov_solve
+    from .binding import (Ctx, ov_eigs, ov_get_stats, ov_reset_stats, ov_set_profiling, ov_sign_apply, ov_solve,
+                          ov_solve_gmresr)
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--lattice", default="24,24,24,48")
@@ -30,6 +35,9 @@ def main(argv=None):
     ap.add_argument("--applies", type=int, default=3)
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--solve", action="store_true")
+    ap.add_argument("--gmresr", action="store_true")
+    ap.add_argument("--eigs-tol", type=float, default=None)
+    ap.add_argument("--profile-range", action="store_true")
     ap.add_argument("--mu", type=float, default=0.02)
     ap.add_argument("--profile", action="store_true",
                     help="time the recurrence's stencil launches with CUDA events (profiling mode 2) after one "
@@ -41,12 +49,20 @@ def main(argv=None):
     links = torch.from_numpy(inputs.gauge_links(dims, seed=1003)).cuda()
     psi = torch.from_numpy(inputs.gaussian_source(dims, seed=2003, nrhs=args.nrhs)).cuda()
     evals, evecs = None, None
-    if args.n_ev > 0:
+    lo, hi = args.lo, args.hi
+    if args.n_ev > 0 and args.eigs_tol is not None:
+        ev = torch.zeros((args.n_ev + 1,) + fshape, dtype=torch.complex128, device="cuda")
+        with Ctx(dims, links, "fp32" if args.prec != "fp64" else "fp64") as c:
+            evals, hi = ov_eigs(c.handle, args.n_ev + 1, args.eigs_tol, 3000, ev)
+        lo = float(abs(evals[args.n_ev]))
+        evals, evecs = evals[:args.n_ev].copy(), ev[:args.n_ev].contiguous()
+        del ev
+    elif args.n_ev > 0:
         evecs = torch.zeros((args.n_ev,) + fshape, dtype=torch.complex128, device="cuda")
         with Ctx(dims, links, "fp32" if args.prec != "fp64" else "fp64") as c:
             evals, _ = ov_eigs(c.handle, args.n_ev, 1e-12, 1, evecs, allow_not_converged=True)
     with Ctx(dims, links, args.prec) as c:
-        c.sign_config(args.order, args.lo, args.hi, evals, evecs)
+        c.sign_config(args.order, lo, hi, evals, evecs)
         out = torch.empty_like(psi)
         if args.profile and not args.solve:
             ov_sign_apply(c.handle, psi, out, args.nrhs)  # tunes the stencil shape for nrhs
@@ -54,22 +70,31 @@ def main(argv=None):
             ov_reset_stats(c.handle)
             ov_set_profiling(c.handle, 2)
         torch.cuda.synchronize()
+        if args.profile_range:
+            torch.cuda.profiler.start()
         t0 = time.perf_counter()
         for _ in range(args.applies):
             if args.solve:
                 it, res = ov_solve(c.handle, args.mu, 1e-10, 20000, psi, out, args.nrhs, allow_not_converged=True)
                 print(f"solve: {it} iterations, true residual {res:.3e}")
+            elif args.gmresr:
+                it, res = ov_solve_gmresr(c.handle, args.mu, 1e-10, 100000, psi, out, args.nrhs,
+                                          allow_not_converged=True)
+                print(f"gmresr: {it} SUMR iterations, true residual {res:.3e}")
             else:
                 ov_sign_apply(c.handle, psi, out, args.nrhs)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        if args.profile_range:
+            torch.cuda.profiler.stop()
         if args.profile and not args.solve:
             ov_set_profiling(c.handle, 0)
             st = ov_get_stats(c.handle)
             per = st["dslash_ms"] / max(1, st["dslash_timed"]) * 1e3
             print(f"stencil: {per:.2f} us per launch ({per / args.nrhs:.2f} per RHS) over {st['dslash_timed']} "
                   f"recurrence launches", flush=True)
-        print(f"{args.applies} x {'solve' if args.solve else 'sign apply'} ({args.prec}, {args.lattice}, "
+        what = "solve" if args.solve else "gmresr solve" if args.gmresr else "sign apply"
+        print(f"{args.applies} x {what} ({args.prec}, {args.lattice}, "
               f"order {args.order}, n_ev {args.n_ev}, nrhs {args.nrhs}): {dt / args.applies * 1e3:.2f} ms each; "
               f"stats {ov_get_stats(c.handle)}", flush=True)
 
