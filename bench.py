@@ -11,8 +11,11 @@ Workload (the 24^3 x 48 lattice the headline metric is quoted on):
 
 Also reported: the stencil's achieved HBM bandwidth (algorithmic bytes over
 its CUDA-event-timed launches inside the timed region), the same metric end
-to end through host buffers, sign(K) applies/s in every precision, and the
-time to a 1e-10 solve of D^dagger D (mixed precision; FP64 with --fp64-solve).
+to end through host buffers, sign(K) applies/s in every precision, the time
+to a 1e-10 solve of D^dagger D (mixed precision; FP64 with --fp64-solve), the
+chiral-sector solve of a point source, the GMRESR solve of D x = b (and of
+the 12 point sources with --batched-solve), 3 steps of over-improved stout
+smearing, the 16^3 x 32 FP32-operator solve and the gradient.
 
 --impl reference times the FP64 CPU oracle (the only reference this method
 has) on a bounded sample of the same workload.
