@@ -67,7 +67,8 @@ typedef enum {
   OV_ERR_NOMEM = 2,         /* device allocation failed */
   OV_ERR_CUDA = 3,          /* a CUDA call or kernel launch failed */
   OV_ERR_NOT_CONVERGED = 4, /* solver hit maxit; best x and its residual are still returned */
-  OV_ERR_STATE = 5          /* call needs ov_sign_config first */
+  OV_ERR_STATE = 5,         /* call needs ov_sign_config first */
+  OV_ERR_NONFINITE = 6      /* (output checks on) an output vector holds NaN or Inf */
 } ov_status;
 
 typedef enum { OV_FP64 = 0, OV_FP32 = 1, OV_MIXED_FP16 = 2, OV_MIXED_BF16 = 3 } ov_prec;
@@ -251,6 +252,15 @@ ov_status ov_sign_poly_grad(ov_ctx* ctx, int order, double lo, double hi, const 
  * Chebyshev recurrence (their summed time including the short gaps between
  * them; other stencil launches are not timed); 0: off (default). */
 ov_status ov_set_profiling(ov_ctx* ctx, int on);
+
+/* Output checks for debugging: with on != 0 every call that returns vectors
+ * (ov_wilson, ov_kernel, ov_sign_apply, ov_sign, ov_overlap, the solvers,
+ * ov_sumr, ov_eigs) first sums the squares of its output in FP64 on the
+ * device and fails with OV_ERR_NONFINITE, writing nothing, when that sum is
+ * NaN or Inf (one extra reduction pass and a read-back per call).  Off by
+ * default; OV_CHECKS=1 in the environment turns it on for every context
+ * created afterwards.  Errors: OV_ERR_INVALID (null ctx). */
+ov_status ov_set_checks(ov_ctx* ctx, int on);
 
 ov_status ov_get_stats(const ov_ctx* ctx, ov_stats* out);
 ov_status ov_reset_stats(ov_ctx* ctx);

@@ -19,12 +19,12 @@ import numpy as np
 
 from .build import LIB_PATH
 
-OV_OK, OV_ERR_INVALID, OV_ERR_NOMEM, OV_ERR_CUDA, OV_ERR_NOT_CONVERGED, OV_ERR_STATE = range(6)
+OV_OK, OV_ERR_INVALID, OV_ERR_NOMEM, OV_ERR_CUDA, OV_ERR_NOT_CONVERGED, OV_ERR_STATE, OV_ERR_NONFINITE = range(7)
 OV_FP64, OV_FP32, OV_MIXED_FP16, OV_MIXED_BF16 = range(4)
 OV_C128, OV_C64 = range(2)
 PRECISIONS = {"fp64": OV_FP64, "fp32": OV_FP32, "fp16": OV_MIXED_FP16, "bf16": OV_MIXED_BF16}
 STATUS_NAMES = {0: "OV_OK", 1: "OV_ERR_INVALID", 2: "OV_ERR_NOMEM", 3: "OV_ERR_CUDA",
-                4: "OV_ERR_NOT_CONVERGED", 5: "OV_ERR_STATE"}
+                4: "OV_ERR_NOT_CONVERGED", 5: "OV_ERR_STATE", 6: "OV_ERR_NONFINITE"}
 
 
 class OverlapError(RuntimeError):
@@ -75,6 +75,7 @@ _SIGNATURES = {
     "ov_get_stats": [_vp, ctypes.POINTER(ov_stats)],
     "ov_reset_stats": [_vp],
     "ov_set_profiling": [_vp, _i],
+    "ov_set_checks": [_vp, _i],
     "ov_wilson_noalloc": [ctypes.POINTER(_i), _vp, _vp, _vp, _i, _i, _i, _vp],
     "ov_stout_smear": [ctypes.POINTER(_i), _vp, _vp, _d, _d, _i, _vp],
 }
@@ -274,6 +275,11 @@ def ov_stout_smear(dims, links_in, links_out, rho=0.1, eps=-0.25, steps=3, strea
 def ov_set_profiling(ctx, on):
     """on: 0 off, 1 (or True) every stencil launch, 2 the recurrence as one bracket (see overlap.h)."""
     return _check(lib().ov_set_profiling(ctx, 2 if on == 2 else int(bool(on))), ctx)
+
+
+def ov_set_checks(ctx, on):
+    """Scan every vector output for NaN / Inf (see overlap.h)."""
+    return _check(lib().ov_set_checks(ctx, int(bool(on))), ctx)
 
 
 def ov_reset_stats(ctx):

@@ -68,6 +68,7 @@ ov_status ov_create(ov_ctx** ctx, const int dims[4], const void* links, ov_prec 
   c->m_w = m_w;
   c->prec = prec;
   c->st = static_cast<cudaStream_t>(cuda_stream);
+  if (const char* chk = std::getenv("OV_CHECKS")) c->checks = std::atoi(chk) != 0;
   {
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess)
@@ -238,6 +239,12 @@ ov_status ov_set_profiling(ov_ctx* c, int on) {
     prof_collect(c);
   }
   c->prof = (on == 2) ? 2 : (on ? 1 : 0);
+  return OV_OK;
+}
+
+ov_status ov_set_checks(ov_ctx* c, int on) {
+  if (!c) return OV_ERR_INVALID;
+  c->checks = on != 0;
   return OV_OK;
 }
 

@@ -196,6 +196,13 @@ ov_status pack_input(ov_ctx* c, Inst& I, const void* in, int nrhs, ov_dtype dt, 
 }
 
 ov_status unpack_output(ov_ctx* c, Inst& I, const void* src, void* out, int nrhs, ov_dtype dt) {
+  if (c->checks) {  // a NaN or Inf anywhere makes the sum of squares non-finite
+    launch_norm2_partial(I.pv, src, c->g.V, nrhs, c->d_partial.as<double2>(), c->st);
+    OV_TRY(launched(c));
+    double2 n2;
+    OV_TRY(read_reduced(c, c->d_partial.as<double2>(), 1, &n2));
+    if (!std::isfinite(n2.x)) return fail(c, OV_ERR_NONFINITE, "output holds NaN or Inf values (checks are on)");
+  }
   void* dout;
   bool staged;
   const size_t bytes = iface_bytes(c->g, nrhs, dt);

@@ -86,6 +86,9 @@ struct ov_ctx {
   int h_scalars_n = 0;
   int* h_stencil_err = nullptr;  // mapped pinned flag of the slab stencil (device view d_stencil_err)
   int* d_stencil_err = nullptr;
+  // output checks (ov_set_checks / OV_CHECKS=1): every vector output is
+  // scanned for NaN / Inf before it is handed back
+  bool checks = false;
   // solver controls
   double inner_tol = 1e-5;
   int max_outer = 30;
