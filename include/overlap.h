@@ -262,6 +262,14 @@ ov_status ov_set_profiling(ov_ctx* ctx, int on);
  * created afterwards.  Errors: OV_ERR_INVALID (null ctx). */
 ov_status ov_set_checks(ov_ctx* ctx, int on);
 
+/* True relative residual history of the last solve (ov_solve,
+ * ov_solve_chiral, ov_solve_gmresr): the largest over the RHS after each
+ * FP64 defect-correction pass, recomputed with the FP64 operator.  Copies up
+ * to max_len values into out (host) and sets *len (may be NULL) to the
+ * number of passes.  Errors: OV_ERR_INVALID (null ctx, max_len < 0, or null
+ * out with max_len > 0). */
+ov_status ov_get_residual_history(const ov_ctx* ctx, double* out, int max_len, int* len);
+
 ov_status ov_get_stats(const ov_ctx* ctx, ov_stats* out);
 ov_status ov_reset_stats(ov_ctx* ctx);
 

@@ -76,6 +76,7 @@ _SIGNATURES = {
     "ov_reset_stats": [_vp],
     "ov_set_profiling": [_vp, _i],
     "ov_set_checks": [_vp, _i],
+    "ov_get_residual_history": [_vp, ctypes.POINTER(_d), _i, ctypes.POINTER(_i)],
     "ov_wilson_noalloc": [ctypes.POINTER(_i), _vp, _vp, _vp, _i, _i, _i, _vp],
     "ov_stout_smear": [ctypes.POINTER(_i), _vp, _vp, _d, _d, _i, _vp],
 }
@@ -275,6 +276,15 @@ def ov_stout_smear(dims, links_in, links_out, rho=0.1, eps=-0.25, steps=3, strea
 def ov_set_profiling(ctx, on):
     """on: 0 off, 1 (or True) every stencil launch, 2 the recurrence as one bracket (see overlap.h)."""
     return _check(lib().ov_set_profiling(ctx, 2 if on == 2 else int(bool(on))), ctx)
+
+
+def ov_get_residual_history(ctx):
+    """Largest true relative residual after each FP64 pass of the last solve."""
+    n = _i(0)
+    _check(lib().ov_get_residual_history(ctx, None, 0, ctypes.byref(n)), ctx)
+    buf = (_d * max(1, n.value))()
+    _check(lib().ov_get_residual_history(ctx, buf, n.value, ctypes.byref(n)), ctx)
+    return [buf[i] for i in range(n.value)]
 
 
 def ov_set_checks(ctx, on):

@@ -242,6 +242,14 @@ ov_status ov_set_profiling(ov_ctx* c, int on) {
   return OV_OK;
 }
 
+ov_status ov_get_residual_history(const ov_ctx* c, double* out, int max_len, int* len) {
+  if (!c || max_len < 0 || (max_len > 0 && !out)) return OV_ERR_INVALID;
+  const int n = (int)c->res_history.size();
+  for (int i = 0; i < std::min(n, max_len); ++i) out[i] = c->res_history[i];
+  if (len) *len = n;
+  return OV_OK;
+}
+
 ov_status ov_set_checks(ov_ctx* c, int on) {
   if (!c) return OV_ERR_INVALID;
   c->checks = on != 0;

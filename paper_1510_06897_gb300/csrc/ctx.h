@@ -101,6 +101,7 @@ struct ov_ctx {
   std::vector<double> coef_relaxed;
   double relaxed_key[4] = {0, 0, 0, 0};
   ov_stats stats{};
+  std::vector<double> res_history;  // largest true relative residual after each FP64 pass of the last solve
   std::string err;
   // stencil profiling (ov_set_profiling): 1 = an event pair around every
   // stencil launch, 2 = one pair around each run of back-to-back stencil

@@ -272,6 +272,7 @@ static ov_status gmresr_core(ov_ctx* c, double mu, double tol, int maxit, const 
   c->stats.gmresr_order = (int)c->coef_relaxed.size() - 1;
   c->stats.inner_iterations = 0;
   c->stats.outer_iterations = 0;
+  c->res_history.clear();
   c->stats.gcr_iterations = 0;
   Inst& H = c->hi;
   Inst& I = (c->prec == OV_FP64) ? c->hi : c->lo;
@@ -335,6 +336,7 @@ static ov_status gmresr_core(ov_ctx* c, double mu, double tol, int maxit, const 
       rn[r] = std::sqrt(n2);
       res[r] = rhs_n[r] > 0 ? rn[r] / rhs_n[r] : 0.0;
     }
+    c->res_history.push_back(*std::max_element(res.begin(), res.end()));
   }
   if (!ok) {
     double worst = 0;

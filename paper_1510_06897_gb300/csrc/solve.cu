@@ -90,6 +90,7 @@ ov_status solve_core(ov_ctx* c, double mu, int chirality, double tol, int maxit,
   if (!c->configured) return fail(c, OV_ERR_STATE, "sign(K) not configured: call ov_sign_config first");
   c->stats.inner_iterations = 0;
   c->stats.outer_iterations = 0;
+  c->res_history.clear();
   Inst& H = c->hi;
   // inner solver: FP64 itself, or the context-precision operator
   Inst& I = (c->prec == OV_FP64) ? c->hi : c->lo;
@@ -165,6 +166,7 @@ ov_status solve_core(ov_ctx* c, double mu, int chirality, double tol, int maxit,
       rn[r] = std::sqrt(n2);
       res[r] = rhs_n[r] > 0 ? rn[r] / rhs_n[r] : 0.0;
     }
+    c->res_history.push_back(*std::max_element(res.begin(), res.end()));
   }
   if (!ok) {
     double worst = 0;

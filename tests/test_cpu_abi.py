@@ -92,6 +92,7 @@ def test_stout_smear_rejects_bad_arguments_before_device_work(lib):
     assert b"extent" in lib.ov_last_error(None) or b"steps" in lib.ov_last_error(None)
     assert lib.ov_get_stats(None, None) == binding.OV_ERR_INVALID
     assert lib.ov_set_checks(None, 1) == binding.OV_ERR_INVALID
+    assert lib.ov_get_residual_history(None, None, 0, None) == binding.OV_ERR_INVALID
 
 
 def test_binding_dtype_codes():
