@@ -34,17 +34,22 @@ def test_stencil_metrics_arithmetic():
 
 
 def test_ncu_traffic_is_keyed_to_the_stencil_sources(tmp_path, monkeypatch):
-    orig = bench.ncu_traffic("fp16")
-    assert orig is not None  # the committed capture matches the committed sources
+    """The traffic figure is used only while the stencil sources hash to the
+    value recorded beside it."""
+    import hashlib
     root = tmp_path / "repo"
     csrc = root / "paper_1510_06897_gb300" / "csrc"
     csrc.mkdir(parents=True)
     (root / "profiles").mkdir()
+    h = hashlib.sha256()
     for name in ("dslash_kernel.cuh", "spin.cuh", "common.cuh"):
         shutil.copy(os.path.join(bench.ROOT, "paper_1510_06897_gb300", "csrc", name), csrc / name)
-    shutil.copy(os.path.join(bench.ROOT, "profiles", "dslash_24x24x24x48.md"), root / "profiles")
+        h.update((csrc / name).read_bytes())
+    (root / "profiles" / "dslash_24x24x24x48.md").write_text(
+        f"    source_sha256_16: {h.hexdigest()[:16]}\n    traffic_bytes_per_site_fp16: 123.4\n")
     monkeypatch.setattr(bench, "ROOT", str(root))
-    assert bench.ncu_traffic("fp16") == orig
+    assert bench.ncu_traffic("fp16") == pytest.approx(123.4)
+    assert bench.ncu_traffic("fp32") is None  # no line for it
     with open(csrc / "spin.cuh", "a") as f:
         f.write("\n// changed\n")
     assert bench.ncu_traffic("fp16") is None
