@@ -128,6 +128,16 @@ def overlap_sumr(links, b, mu, cfg, maxit, tol=0.0, m_w=M_W, antiperiodic_t=Fals
     return sumr(u_op, zeta_of(mu), 2.0 * b / (1.0 - mu), maxit, tol)
 
 
+def _orthogonalise(c, u, us, cs):
+    """Modified Gram-Schmidt of c against the kept c_i, the same combination
+    applied to u."""
+    for ui, ci in zip(us, cs):
+        beta = inner(ci, c)
+        c = c - beta * ci
+        u = u - beta * ui
+    return c, u
+
+
 def gcr(apply_a, precond, b, tol, max_outer, max_dirs=None):
     """GCR with a (possibly varying) preconditioner precond(r) ~ A^{-1} r.
 
@@ -139,11 +149,7 @@ def gcr(apply_a, precond, b, tol, max_outer, max_dirs=None):
     k = 0
     while k < max_outer and np.sqrt(inner(r, r).real) > tol * nb:
         u = precond(r)
-        c = apply_a(u)
-        for ui, ci in zip(us, cs):
-            beta = inner(ci, c)
-            c = c - beta * ci
-            u = u - beta * ui
+        c, u = _orthogonalise(apply_a(u), u, us, cs)
         n = np.sqrt(inner(c, c).real)
         c, u = c / n, u / n
         g = inner(c, r)

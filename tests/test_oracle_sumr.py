@@ -15,7 +15,8 @@ dense linear algebra:
   * GMRESR with a relaxed (low-order) inner sign converges to the dense
     solve of the accurate polynomial operator;
   * planted mistakes (a conjugated coefficient, a dropped shift term, the
-    wrong sign of the shift) each fail one of these.
+    wrong sign of the shift, GCR without orthogonalisation) each fail one of
+    these.
 """
 import numpy as np
 import pytest
@@ -209,3 +210,9 @@ def test_planted_shift_sign_fails(monkeypatch, prob):
     x, _, _ = sumr_mod.sumr(lambda v: u @ v, sumr_mod.zeta_of(mu), 2.0 * b / (1.0 - mu), 400, 1e-12)
     d = 0.5 * ((1 + mu) * np.eye(n) + (1 - mu) * u)
     assert _rel(x, np.linalg.solve(d, b)) > 1e-3
+
+
+def test_planted_missing_orthogonalisation_fails(monkeypatch):
+    """GCR without the Gram-Schmidt step against the kept directions."""
+    monkeypatch.setattr(sumr_mod, "_orthogonalise", lambda c, u, us, cs: (c, u))
+    assert not _gcr_identity_ok()
