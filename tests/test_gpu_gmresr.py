@@ -133,3 +133,29 @@ def test_gmresr_rejects_bad_arguments(setup):
             with pytest.raises(OverlapError) as e:
                 ov_set_gmresr_params(c.handle, *args)
             assert e.value.status == 1
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_gmresr_ragged_antiperiodic_three_rhs(prec):
+    """3x2x5x4 (volume not a multiple of any block), antiperiodic t, 6 dense
+    eigenpairs deflated, order 20, 3 right-hand sides in one call."""
+    prob = small_problem((3, 2, 5, 4), seed=4301, n_ev=6, antiperiodic=True)
+    order, mu = 20, 0.05
+    cfg = overlap.SignConfig(chebyshev.coefficients(order, prob["a"], prob["b"]), prob["a"], prob["b"],
+                             prob["evals"], prob["evecs"])
+    vol = inputs.volume(prob["dims"])
+    w, v = dense.sorted_eigh(prob["kmat"])
+    s = chebyshev.p_scalar(cfg.coeffs, cfg.a, cfg.b, w)
+    s[:6] = np.where(w[:6] >= 0, 1.0, -1.0)
+    dmat = 0.5 * ((1 + mu) * np.eye(12 * vol) + (1 - mu) * dense.gamma5_matrix(vol) @ ((v * s) @ v.conj().T))
+    b = inputs.gaussian_source(prob["dims"], seed=9506, nrhs=3)
+    with Ctx(prob["dims"], dev(prob["links"]), prec, antiperiodic_t=True) as c:
+        c.sign_config(order, prob["a"], prob["b"], prob["evals"], dev(prob["evecs"]))
+        x, it, res = c.solve_gmresr(dev(b), mu)
+    x = host(x)
+    assert res <= 1e-10
+    for r in range(3):
+        rr = b[r] - overlap.overlap(prob["links"], x[r], mu, cfg, antiperiodic_t=True)
+        assert np.linalg.norm(rr) <= 2e-10 * np.linalg.norm(b[r]), r
+        want = np.linalg.solve(dmat, b[r].ravel())
+        assert np.linalg.norm(x[r].ravel() - want) <= 1e-8 * np.linalg.norm(want), r
