@@ -521,6 +521,7 @@ def extras(args, ctx, links_d, a, b, evals, evecs, psi, vol):
                                      x_cg=x_cg)
     res["solve_1e-10"] = solves
     res["stout_smearing"] = smear_timing(links_d)
+    res["paper_lattices_wilson"] = paper_wilson_timing()
     res["solve_16x16x16x32_fp32"] = solve_16_timing()
     res["gradient"] = gradient_timing()
     return res
@@ -584,6 +585,42 @@ def gmresr_batched_timing(links_d, a, b, evals, evecs, src, prec):
     return {"precision": prec, "nrhs": int(src.shape[0]), "seconds": dt, "sumr_iterations": it,
             "relaxed_order": st["gmresr_order"], "gcr_steps": st["gcr_iterations"],
             "fp64_passes": st["outer_iterations"], "true_rel_resid_D": r}
+
+
+# The paper's Wilson-matrix times on its own lattices (Table 4, one GTX Titan,
+# precision not stated), quoted beside ours for context only.
+PAPER_WILSON_MS = {"8x8x8x32": 0.248, "20x20x20x64": 6.759}
+
+
+def paper_wilson_timing():
+    """D_W (ov_wilson's stencil launch, CUDA events around each launch) on the
+    paper's two lattices, FP64 / FP32 / FP16 storage, seeded synthetic links."""
+    import torch
+    from paper_1510_06897_gb300 import inputs
+    from paper_1510_06897_gb300.binding import Ctx, ov_get_stats, ov_reset_stats, ov_set_profiling, ov_wilson
+    out = {}
+    for dims in ((8, 8, 8, 32), (20, 20, 20, 64)):
+        key = "x".join(str(d) for d in dims)
+        links = torch.from_numpy(inputs.gauge_links(dims, seed=SEED_LINKS)).cuda()
+        psi = torch.from_numpy(inputs.gaussian_source(dims, seed=SEED_SRC)).cuda()
+        res = {"paper_gtx_titan_ms": PAPER_WILSON_MS[key]}
+        for prec in ("fp64", "fp32", "fp16"):
+            with Ctx(dims, links, prec) as c:
+                y = torch.empty_like(psi)
+                for _ in range(3):
+                    ov_wilson(c.handle, psi, y, 1)
+                torch.cuda.synchronize()
+                ov_reset_stats(c.handle)
+                ov_set_profiling(c.handle, 1)
+                for _ in range(20):
+                    ov_wilson(c.handle, psi, y, 1)
+                torch.cuda.synchronize()
+                ov_set_profiling(c.handle, 0)
+                st = ov_get_stats(c.handle)
+            res[f"{prec}_stencil_ms"] = st["dslash_ms"] / max(1, st["dslash_timed"])
+        out[key] = res
+        del links, psi
+    return out
 
 
 def _plaquette(u):
