@@ -384,7 +384,10 @@ def main():
             "roofline": roofline, "e2e": e2e, "gpu_launches": st["kernel_launches"], "clocks": clk}
 
     if rank == 0 and not args.no_extras:
-        line["extras"] = extras(args, ctx, links_d, a, b, evals40, evecs40, psi, vol)
+        try:
+            line["extras"] = extras(args, ctx, links_d, a, b, evals40, evecs40, psi, vol)
+        except Exception as e:  # a failing extra must not cost the headline line
+            line["extras"] = {"error": f"{type(e).__name__}: {e}"}
     ctx.close()
     if rank == 0 and world == 1 and not args.no_cpu:
         evh = evecs40[:4].cpu().numpy()
@@ -489,8 +492,8 @@ def extras(args, ctx, links_d, a, b, evals, evecs, psi, vol):
         solves["batched_12_point_sources"] = {
             "precision": args.prec, "seconds": dt, "iterations": it, "outer": st["outer_iterations"],
             "true_rel_resid": r, "fp64_estimate_seconds": 12 * 2 * solves[args.prec]["iterations"] * fp64_apply}
-        solves["batched_12_point_sources_gmresr"] = gmresr_batched_timing(links_d, a, b, evals, evecs, src,
-                                                                          args.prec)
+        solves["batched_12_point_sources_gmresr"] = _guarded(gmresr_batched_timing, links_d, a, b, evals, evecs,
+                                                             src, args.prec)
     # chiral point source (spin 0, colour 0 at the origin: chirality +1): D^-1 b
     # from the chiral-sector solve (one sign apply per iteration) + one D^dagger,
     # against the D^dagger D solve of the same source
@@ -517,14 +520,23 @@ def extras(args, ctx, links_d, a, b, evals, evecs, psi, vol):
                             "sign_applies": st["sign_applies"], "true_rel_resid": r}
     chiral["speedup"] = chiral["normal_equations"]["seconds"] / chiral["chiral_sector"]["seconds"]
     solves["chiral_point_source"] = chiral
-    solves["gmresr"] = gmresr_timing(links_d, a, b, evals, evecs, psi, args.prec, solves[args.prec]["seconds"],
-                                     x_cg=x_cg)
+    solves["gmresr"] = _guarded(gmresr_timing, links_d, a, b, evals, evecs, psi, args.prec,
+                                solves[args.prec]["seconds"], x_cg=x_cg)
     res["solve_1e-10"] = solves
-    res["stout_smearing"] = smear_timing(links_d)
-    res["paper_lattices_wilson"] = paper_wilson_timing()
-    res["solve_16x16x16x32_fp32"] = solve_16_timing()
-    res["gradient"] = gradient_timing()
+    res["stout_smearing"] = _guarded(smear_timing, links_d)
+    res["paper_lattices_wilson"] = _guarded(paper_wilson_timing)
+    res["solve_16x16x16x32_fp32"] = _guarded(solve_16_timing)
+    res["gradient"] = _guarded(gradient_timing)
     return res
+
+
+def _guarded(fn, *args, **kwargs):
+    """fn's result, or the error it raised (independent extras do not take
+    the others down with them)."""
+    try:
+        return fn(*args, **kwargs)
+    except Exception as e:
+        return {"error": f"{type(e).__name__}: {e}"}
 
 
 def gmresr_timing(links_d, a, b, evals, evecs, psi, prec, cg_seconds=None, settings=((0, 0.1),), x_cg=None):
