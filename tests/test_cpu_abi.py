@@ -102,3 +102,42 @@ def test_binding_dtype_codes():
         binding._dtype_code(np.zeros(2, np.float64))
     with pytest.raises(ValueError):
         binding._ptr(np.zeros((4, 4), np.complex128)[:, ::2])
+
+
+def _prototypes():
+    """name -> list of parameter declarations, parsed from include/overlap.h."""
+    text = open(os.path.join(ROOT, "include", "overlap.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    out = {}
+    for m in re.finditer(r"\b(?:ov_status|const char\s*\*)\s*(ov_[a-z_]+)\s*\(([^)]*)\)\s*;", text):
+        params = [p.strip() for p in m.group(2).replace("\n", " ").split(",") if p.strip() and p.strip() != "void"]
+        out[m.group(1)] = params
+    return out
+
+
+def _kind(decl):
+    """'p' for a pointer parameter (including arrays), 'd' for double, 'i' for int / enum."""
+    if "*" in decl or "[" in decl:
+        return "p"
+    if re.search(r"\bdouble\b", decl):
+        return "d"
+    return "i"
+
+
+def _ctype_kind(t):
+    if t is ctypes.c_void_p or (isinstance(t, type) and issubclass(t, ctypes._Pointer)):
+        return "p"
+    if t is ctypes.c_double:
+        return "d"
+    return "i"
+
+
+def test_binding_signatures_match_the_header():
+    protos = _prototypes()
+    assert len(protos) >= len(binding._SIGNATURES)
+    for name, args in binding._SIGNATURES.items():
+        assert name in protos, name
+        want = [_kind(p) for p in protos[name]]
+        got = [_ctype_kind(t) for t in args]
+        assert got == want, (name, got, want)
