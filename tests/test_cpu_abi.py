@@ -141,3 +141,12 @@ def test_binding_signatures_match_the_header():
         want = [_kind(p) for p in protos[name]]
         got = [_ctype_kind(t) for t in args]
         assert got == want, (name, got, want)
+
+
+def test_stats_struct_matches_the_header():
+    text = open(os.path.join(ROOT, "include", "overlap.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct\s*\{([^}]*)\}\s*ov_stats\s*;", text).group(1)
+    fields = re.findall(r"(long long|double|int)\s+([a-z_0-9]+)\s*;", body)
+    ctypes_of = {"long long": ctypes.c_longlong, "double": ctypes.c_double, "int": ctypes.c_int}
+    assert [(n, ctypes_of[t]) for t, n in fields] == list(binding.ov_stats._fields_)
