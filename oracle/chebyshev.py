@@ -20,9 +20,9 @@ evaluation order from the library's backward (Clenshaw) sweep:
   T_0 = v,  T_1 = Z v,  T_{j+1} = 2 Z T_j - T_{j-1},  Z = alpha K^2 + beta,
   alpha = 2/(b^2 - a^2),  beta = -(b^2 + a^2)/(b^2 - a^2).
 
-Pinned by: interpolation at the nodes, the free-field scalar closed form,
-and dense eigendecomposition within the scalar error bound
-(tests/test_oracle_sign.py).
+Pinned by: interpolation at the nodes, NumPy's Chebyshev interpolation of
+the same function, the free-field scalar closed form, and dense
+eigendecomposition within the scalar error bound (tests/test_oracle_sign.py).
 """
 import numpy as np
 

@@ -118,3 +118,15 @@ def test_sign_is_hermitian_and_involutive(prob):
     assert abs(lhs - rhs) < 1e-12 * abs(lhs)
     s2 = overlap.sign_apply(prob["links"], s_psi, cfg)
     assert _rel(s2, psi) < 1e-8
+
+
+@pytest.mark.parametrize("order,a,b", [(8, 0.3, 6.5), (40, 0.45, 6.5), (256, 0.2, 6.6)])
+def test_coefficients_match_numpy_chebinterpolate(order, a, b):
+    """The coefficients equal NumPy's interpolant at the Chebyshev points of
+    the first kind in z (NumPy keeps c_0 whole; the oracle's series halves it)."""
+    from numpy.polynomial import chebyshev as npcheb
+    c = chebyshev.coefficients(order, a, b)
+    f = lambda z: (((b * b - a * a) * z + b * b + a * a) / 2) ** -0.5  # noqa: E731
+    want = npcheb.chebinterpolate(f, order)
+    assert np.max(np.abs(c[1:] - want[1:])) < 1e-13
+    assert abs(c[0] / 2 - want[0]) < 1e-13
