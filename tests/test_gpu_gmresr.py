@@ -159,3 +159,18 @@ def test_gmresr_ragged_antiperiodic_three_rhs(prec):
         assert np.linalg.norm(rr) <= 2e-10 * np.linalg.norm(b[r]), r
         want = np.linalg.solve(dmat, b[r].ravel())
         assert np.linalg.norm(x[r].ravel() - want) <= 1e-8 * np.linalg.norm(want), r
+
+
+def test_sumr_fp64_three_rhs_larger_mu(setup):
+    """Same iterates as the oracle for 3 RHS at mu = 0.3 after 8 steps (FP64
+    batched deflation path)."""
+    prob, cfg = setup
+    b = inputs.gaussian_source(prob["dims"], seed=9507, nrhs=3)
+    mu, k = 0.3, 8
+    with _ctx(prob, "fp64") as c:
+        x, it, est = c.sumr(dev(b), mu, 0.0, k)
+    x = host(x)
+    assert it == k
+    for r in range(3):
+        want, _, _ = sumr.overlap_sumr(prob["links"], b[r], mu, cfg, k)
+        assert np.linalg.norm(x[r] - want) <= 1e-10 * np.linalg.norm(want), r
