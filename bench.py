@@ -577,7 +577,30 @@ def gmresr_timing(links_d, a, b, evals, evecs, psi, prec, cg_seconds=None, setti
                 "speedup_vs_cg_normal_equations": (cg_seconds / dt) if cg_seconds else None,
                 "rel_diff_to_cg_solution": ((torch.linalg.vector_norm(x - x_cg) / torch.linalg.vector_norm(x_cg)).item()
                                             if x_cg is not None else None)}
+    if prec in ("fp16", "bf16"):  # the GCR level on an FP32 copy of the operator
+        out["fp32_gcr_level"] = _guarded(_gmresr_fp32_level, links_d, a, b, evals, evecs, psi, prec, cg_seconds)
     return out
+
+
+def _gmresr_fp32_level(links_d, a, b, evals, evecs, psi, prec, cg_seconds):
+    import torch
+    from paper_1510_06897_gb300.binding import Ctx, ov_enable_fp32_operator, ov_get_stats, ov_solve_gmresr
+    with Ctx(DIMS, links_d, prec) as c:
+        t0 = time.perf_counter()
+        ov_enable_fp32_operator(c.handle, links_d)
+        c.sign_config(ORDER, a, b, evals, evecs)
+        setup = time.perf_counter() - t0
+        x = torch.empty_like(psi)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it, r = ov_solve_gmresr(c.handle, MU, 1e-10, 100000, psi, x, 1, allow_not_converged=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st = ov_get_stats(c.handle)
+    return {"precision": f"{prec} SUMR, fp32 GCR", "seconds": dt, "setup_s (FP32 copy + configuration)": setup,
+            "sumr_iterations": it, "relaxed_order": st["gmresr_order"], "gcr_steps": st["gcr_iterations"],
+            "fp64_passes": st["outer_iterations"], "true_rel_resid_D": r,
+            "speedup_vs_cg_normal_equations": (cg_seconds / dt) if cg_seconds else None}
 
 
 def gmresr_batched_timing(links_d, a, b, evals, evecs, src, prec):

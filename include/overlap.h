@@ -210,6 +210,20 @@ ov_status ov_sumr(ov_ctx* ctx, double mu, double tol, int maxit, const void* b, 
 ov_status ov_solve_gmresr(ov_ctx* ctx, double mu, double tol, int maxit, const void* b, void* x, int nrhs,
                           ov_dtype dtype, int* iters, double* true_rel_resid);
 
+/* An FP32 copy of the operator beside the 16-bit one of an OV_MIXED_FP16 /
+ * OV_MIXED_BF16 context, for ov_solve_gmresr: its GCR level then runs with
+ * this FP32 operator (configured order) while the inner SUMR solves stay on
+ * the 16-bit one, so each FP64 defect-correction pass gains about the FP32
+ * accuracy instead of the 16-bit one and fewer FP64 passes are needed.
+ * links: the field given to ov_create, same layout (host or device).  The
+ * deflation eigenvectors come from the last ov_sign_config (converted from
+ * its FP64 copy) or the next one.  Costs FP32 links, eigenvectors and work
+ * vectors and one stencil autotuning.  No effect on OV_FP64 / OV_FP32
+ * contexts and on a second call (OV_OK).  Errors: OV_ERR_INVALID (null
+ * ctx or links), OV_ERR_NOMEM, OV_ERR_CUDA (the context keeps working without
+ * the FP32 copy). */
+ov_status ov_enable_fp32_operator(ov_ctx* ctx, const void* links);
+
 /* GMRESR controls.  inner_order: Chebyshev order of the relaxed sign of the
  * inner SUMR solves (0, the default: the smallest order whose sign error
  * max |sqrt(y) f_N(y) - 1| on [lo^2, hi^2] is <= 1e-2; never above the

@@ -70,6 +70,7 @@ _SIGNATURES = {
     "ov_sumr": [_vp, _d, _d, _i, _vp, _vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)],
     "ov_solve_gmresr": [_vp, _d, _d, _i, _vp, _vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)],
     "ov_set_gmresr_params": [_vp, _i, _d, _i, _i],
+    "ov_enable_fp32_operator": [_vp, _vp],
     "ov_eigs": [_vp, _i, _d, _i, ctypes.POINTER(_d), _vp, ctypes.POINTER(_d)],
     "ov_sign_poly_grad": [_vp, _i, _d, _d, _vp, _vp, _i],
     "ov_get_stats": [_vp, ctypes.POINTER(ov_stats)],
@@ -226,6 +227,11 @@ def ov_solve_gmresr(ctx, mu, tol, maxit, b, x, nrhs, allow_not_converged=False):
     if not (allow_not_converged and st == OV_ERR_NOT_CONVERGED):
         _check(st, ctx)
     return it.value, res.value
+
+
+def ov_enable_fp32_operator(ctx, links):
+    """FP32 operator beside a 16-bit one, for the GCR level of ov_solve_gmresr (see overlap.h)."""
+    return _check(lib().ov_enable_fp32_operator(ctx, _ptr(links)), ctx)
 
 
 def ov_set_gmresr_params(ctx, inner_order=0, inner_tol=0.1, inner_maxit=1000, max_dirs=12):

@@ -115,6 +115,7 @@ ov_status ov_destroy(ov_ctx* c) {
   }
   c->hi.release();
   c->lo.release();
+  c->mid.release();
   for (cudaEvent_t ev : c->evs) cudaEventDestroy(ev);
   for (DevBuf* b : {&c->d_sgn, &c->d_c, &c->d_partial, &c->d_scalars, &c->d_gram, &c->d_err, &c->stage_in, &c->stage_out, &c->stage_links,
                     &c->o_x, &c->o_r, &c->o_rhs, &c->o_q})
@@ -177,7 +178,7 @@ ov_status ov_sign_config(ov_ctx* c, int order, double lo, double hi, const doubl
     const size_t ib = iface_bytes(c->g, n_ev, OV_C128);
     const void* de;
     OV_TRY(stage_in(c, c->stage_in, evecs, ib, &de));
-    for (Inst* I : {&c->hi, &c->lo}) {
+    for (Inst* I : {&c->hi, &c->lo, &c->mid}) {
       if (!I->active) continue;
       OV_CK(I->evecs.ensure(I->vbytes(c->g.V) * n_ev));
       launch_pack_spinor(I->pv, IF_C128, c->g, de, I->evecs.p, n_ev, 1.0, 0, c->st);

@@ -70,6 +70,7 @@ struct ov_ctx {
   ov_prec prec = OV_FP64;
   Inst hi;  // FP64 operator (always)
   Inst lo;  // operator in the context precision when it is not FP64
+  Inst mid;  // FP32 operator beside a 16-bit one (ov_enable_fp32_operator): the GCR level of GMRESR
   // sign configuration
   bool configured = false;
   int order = 0;

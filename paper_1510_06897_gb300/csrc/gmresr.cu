@@ -164,20 +164,24 @@ ov_status sumr_core(ov_ctx* c, Inst& I, const std::vector<double>& cf, double mu
   return OV_OK;
 }
 
-// GCR on D[mu] e = r0 in instance I (vectors in I.pv), each direction an
-// inner SUMR solve with the relaxed coefficients.  Stops when the updated
-// residual |r| <= tol |r0| for every RHS, or when the inner products reach
-// maxit.  *inner: SUMR products with U; *steps: GCR steps.
-static ov_status gcr_core(ov_ctx* c, Inst& I, const void* r0, void* e, int nrhs, double mu, double tol, int maxit,
-                          int* inner, int* steps) {
+// GCR on D[mu] e = r0 with the operator of instance I (its vectors, in
+// I.pv, hold the residual and the kept directions), each direction an inner
+// SUMR solve with the relaxed coefficients on instance S (S.pv must equal
+// I.pv: the SUMR right-hand side and solution live in I's buffers).  Stops
+// when the updated residual |r| <= tol |r0| for every RHS, or when the inner
+// products reach maxit.  *inner: SUMR products with U; *steps: GCR steps.
+static ov_status gcr_core(ov_ctx* c, Inst& I, Inst& S, const void* r0, void* e, int nrhs, double mu, double tol,
+                          int maxit, int* inner, int* steps) {
   const int64_t V = c->g.V;
   const size_t v1 = I.vbytes(V), vb = v1 * nrhs;
   const int dirs = c->gm_dirs;
+  if (S.pv != I.pv) return fail(c, OV_ERR_INVALID, "GCR and SUMR instances store vectors differently");
   OV_CK(I.gr.ensure(vb));
   OV_CK(I.grhs.ensure(vb));
   OV_CK(I.gu.ensure(vb * dirs));
   OV_CK(I.gc.ensure(vb * dirs));
-  OV_TRY(ensure_sumr(c, I, nrhs));
+  OV_TRY(ensure_work(c, I, nrhs));
+  OV_TRY(ensure_sumr(c, S, nrhs));
   OV_CK(cudaMemsetAsync(e, 0, vb, c->st));
   OV_CK(cudaMemcpyAsync(I.gr.p, r0, vb, cudaMemcpyDeviceToDevice, c->st));
   std::vector<double> rn(nrhs), rn0(nrhs);
@@ -205,7 +209,7 @@ static ov_status gcr_core(ov_ctx* c, Inst& I, const void* r0, void* e, int nrhs,
     }
     int its = 0;
     double est = 0.0;
-    OV_TRY(sumr_core(c, I, c->coef_relaxed, mu, I.grhs.p, u, nrhs, c->gm_tol, std::min(c->gm_maxit, maxit - n_inner),
+    OV_TRY(sumr_core(c, S, c->coef_relaxed, mu, I.grhs.p, u, nrhs, c->gm_tol, std::min(c->gm_maxit, maxit - n_inner),
                      &its, &est));
     n_inner += its;
     // c_k = D[mu] u_k with the accurate order
@@ -275,11 +279,16 @@ static ov_status gmresr_core(ov_ctx* c, double mu, double tol, int maxit, const 
   c->res_history.clear();
   c->stats.gcr_iterations = 0;
   Inst& H = c->hi;
-  Inst& I = (c->prec == OV_FP64) ? c->hi : c->lo;
+  // S: the inner SUMR level (the context precision); I: the GCR level, the
+  // FP32 operator of ov_enable_fp32_operator when a 16-bit context has one
+  Inst& S = (c->prec == OV_FP64) ? c->hi : c->lo;
+  const bool mid = c->mid.active && (c->prec == OV_MIXED_FP16 || c->prec == OV_MIXED_BF16);
+  Inst& I = mid ? c->mid : S;
   const int64_t V = c->g.V;
   const size_t v1 = H.vbytes(V), vb = v1 * nrhs, iv1 = I.vbytes(V);
   OV_TRY(ensure_work(c, H, nrhs));
   OV_TRY(ensure_work(c, I, nrhs));
+  OV_TRY(ensure_work(c, S, nrhs));
   OV_CK(c->o_x.ensure(vb));
   OV_CK(c->o_r.ensure(vb));
   OV_CK(c->o_rhs.ensure(vb));
@@ -318,7 +327,7 @@ static ov_status gmresr_core(ov_ctx* c, double mu, double tol, int maxit, const 
     if (c->prec != OV_FP64) inner = std::max(inner, c->inner_tol);
     inner = std::min(inner, 0.5);
     int its = 0, steps = 0;
-    ov_status s = gcr_core(c, I, I.xin.p, I.cx.p, nrhs, mu, inner, maxit - total, &its, &steps);
+    ov_status s = gcr_core(c, I, S, I.xin.p, I.cx.p, nrhs, mu, inner, maxit - total, &its, &steps);
     total += its;
     c->stats.gcr_iterations += steps;
     if (s != OV_OK && s != OV_ERR_NOT_CONVERGED) return s;
@@ -356,6 +365,35 @@ static ov_status gmresr_core(ov_ctx* c, double mu, double tol, int maxit, const 
 }  // namespace ov
 
 extern "C" {
+
+ov_status ov_enable_fp32_operator(ov_ctx* c, const void* links) {
+  if (!c) return OV_ERR_INVALID;
+  if (!links) return fail(c, OV_ERR_INVALID, "null links");
+  if (c->prec != OV_MIXED_FP16 && c->prec != OV_MIXED_BF16) return OV_OK;  // already FP32 or FP64
+  if (c->mid.active) return OV_OK;
+  const void* dl = nullptr;
+  ov_status s = stage_in(c, c->stage_links, links, (size_t)c->g.V * 4 * 9 * 16, &dl);
+  if (s == OV_OK) s = init_inst(c, c->mid, OP_F32, dl);
+  if (s == OV_OK && c->configured && c->n_ev > 0) {  // eigenvectors from the FP64 copy
+    cudaError_t e = c->mid.evecs.ensure(c->mid.vbytes(c->g.V) * c->n_ev);
+    if (e != cudaSuccess) {
+      s = fail(c, e == cudaErrorMemoryAllocation ? OV_ERR_NOMEM : OV_ERR_CUDA, cudaGetErrorString(e));
+    } else {
+      launch_convert(OP_F64, OP_F32, c->hi.evecs.p, c->mid.evecs.p, c->g.V, c->n_ev, 1.0, 0, c->st);
+      s = launched(c);
+    }
+  }
+  if (s == OV_OK) {
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) s = fail(c, OV_ERR_CUDA, cudaGetErrorString(e));
+  }
+  c->stage_links.release();
+  if (s != OV_OK) {
+    c->mid.release();
+    c->mid.active = false;
+  }
+  return s;
+}
 
 ov_status ov_set_gmresr_params(ov_ctx* c, int inner_order, double inner_tol, int inner_maxit, int max_dirs) {
   if (!c) return OV_ERR_INVALID;

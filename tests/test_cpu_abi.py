@@ -16,7 +16,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     text = open(os.path.join(ROOT, "include", "overlap.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(ov_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(ov_[a-z_0-9]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
@@ -77,6 +77,7 @@ def test_null_context_calls(lib):
     assert lib.ov_sumr(None, 0.1, 1e-10, 10, None, None, 1, 0, None, None) == binding.OV_ERR_INVALID
     assert lib.ov_solve_gmresr(None, 0.1, 1e-10, 10, None, None, 1, 0, None, None) == binding.OV_ERR_INVALID
     assert lib.ov_set_gmresr_params(None, 0, 0.1, 100, 8) == binding.OV_ERR_INVALID
+    assert lib.ov_enable_fp32_operator(None, None) == binding.OV_ERR_INVALID
 
 
 def test_stout_smear_rejects_bad_arguments_before_device_work(lib):
@@ -110,7 +111,7 @@ def _prototypes():
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     text = re.sub(r"//[^\n]*", "", text)
     out = {}
-    for m in re.finditer(r"\b(?:ov_status|const char\s*\*)\s*(ov_[a-z_]+)\s*\(([^)]*)\)\s*;", text):
+    for m in re.finditer(r"\b(?:ov_status|const char\s*\*)\s*(ov_[a-z_0-9]+)\s*\(([^)]*)\)\s*;", text):
         params = [p.strip() for p in m.group(2).replace("\n", " ").split(",") if p.strip() and p.strip() != "void"]
         out[m.group(1)] = params
     return out
