@@ -523,6 +523,7 @@ def extras(args, ctx, links_d, a, b, evals, evecs, psi, vol):
     solves["gmresr"] = _guarded(gmresr_timing, links_d, a, b, evals, evecs, psi, args.prec,
                                 solves[args.prec]["seconds"], x_cg=x_cg)
     res["solve_1e-10"] = solves
+    res["launch_gaps"] = _guarded(launch_gap_timing, ctx, psi, args.prec)
     res["stout_smearing"] = _guarded(smear_timing, links_d)
     res["paper_lattices_wilson"] = _guarded(paper_wilson_timing)
     res["solve_16x16x16x32_fp32"] = _guarded(solve_16_timing)
@@ -656,6 +657,30 @@ def paper_wilson_timing():
         out[key] = res
         del links, psi
     return out
+
+
+def launch_gap_timing(ctx, psi, prec, reps=4):
+    """Stencil time per launch of the recurrence measured two ways on the
+    headline context: one event pair around every launch (kernel time; the
+    extra event records between launches slow the apply itself) and one pair
+    around the 2N back-to-back launches (kernel time plus the gaps between
+    launches).  Their difference bounds what overlapping consecutive
+    launches could save."""
+    import torch
+    from paper_1510_06897_gb300.binding import ov_get_stats, ov_reset_stats, ov_set_profiling, ov_sign_apply
+    out = torch.empty_like(psi)
+    per = {}
+    for mode in (1, 2):
+        ov_reset_stats(ctx.handle)
+        ov_set_profiling(ctx.handle, mode)
+        for _ in range(reps):
+            ov_sign_apply(ctx.handle, psi, out, 1)
+        torch.cuda.synchronize()
+        ov_set_profiling(ctx.handle, 0)
+        st = ov_get_stats(ctx.handle)
+        per[mode] = st["dslash_ms"] / max(1, st["dslash_timed"]) * 1e3
+    return {"precision": prec, "us_per_launch_events_around_each": per[1],
+            "us_per_launch_bracketed_recurrence": per[2], "gap_us_per_launch": per[2] - per[1]}
 
 
 def _plaquette(u):
