@@ -136,7 +136,11 @@ extern "C" ov_status ov_eigs(ov_ctx* c, int n_ev, double tol, int max_iter, doub
   if (n_ev < 1 || n_ev + 8 > mmax) return fail(c, OV_ERR_INVALID, "need 1 <= n_ev <= " + std::to_string(mmax - 8));
   if (!(tol > 0.0) || max_iter < 1) return fail(c, OV_ERR_INVALID, "need tol > 0 and max_iter >= 1");
   const int64_t V = c->g.V;
-  const int m = std::min(mmax, std::max(n_ev + 8, n_ev + n_ev / 2));
+  // block of ~2.5 n_ev (capped by the Gram kernel): a wider block separates
+  // the wanted band from the rest better, so fewer filter sweeps are needed
+  // (counted on a model problem: 20 pairs, block 50 vs 30, half the K
+  // applications)
+  const int m = std::min(mmax, std::max(n_ev + 8, (5 * n_ev) / 2));
   if ((int64_t)m > 12 * V) return fail(c, OV_ERR_INVALID, "block larger than the vector space");
   Inst& I = (c->prec == OV_FP32) ? c->lo : c->hi;  // FP32 or FP64 storage (I.p == I.pv)
   const OpPrec P = I.p;
