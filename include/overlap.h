@@ -242,7 +242,8 @@ ov_status ov_set_gmresr_params(ov_ctx* ctx, int inner_order, double inner_tol, i
  * device).  tol: relative eigen-residual ||K phi - lambda phi|| <= tol * lambda_max.
  * lambda_max_out (may be NULL): an upper bound of |lambda| of K.  max_iter
  * counts filter + Rayleigh-Ritz steps (filter degree 32 on K^2; the
- * environment variable OV_EIGS_DEGREE overrides it, 4 .. 256).
+ * environment variable OV_EIGS_DEGREE overrides it, 4 .. 256) on a block of
+ * max(n_ev + 8, 2.5 n_ev) vectors, at most 64 (so n_ev <= 56).
  * Errors: OV_ERR_INVALID, OV_ERR_NOT_CONVERGED (best pairs returned; also when
  * the filtered block stops being finite, with no pairs written). */
 ov_status ov_eigs(ov_ctx* ctx, int n_ev, double tol, int max_iter, double* evals, void* evecs,
