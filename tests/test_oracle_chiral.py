@@ -1,11 +1,20 @@
 """Pins of the oracle's chiral-sector normal operator (one sign function
-application per CG iteration instead of two)."""
+application per CG iteration instead of two).  The identities are algebraic,
+so they are checked on the 2^3 x 4 lattice (4 deflated pairs), where the
+dense matrices are 384 x 384."""
 import numpy as np
 import pytest
 
 from oracle import cg, chebyshev, dense, overlap
 from paper_1510_06897_gb300 import inputs
 from tests.oracle_fixtures import small_problem
+
+DIMS = (2, 2, 2, 4)
+N_EV = 4
+
+
+def _problem():
+    return small_problem(DIMS, n_ev=N_EV)
 
 
 def _dense_overlap(smat, mu, vol):
@@ -22,7 +31,7 @@ def _proj_matrix(vol, chirality):
 def test_chiral_operator_equals_projected_normal_with_exact_sign(chirality, mu):
     """With the exact dense sign (S^2 = 1): A = P D^dagger D P, built here from
     dense matrices independently of the oracle's operator code."""
-    prob = small_problem()
+    prob = _problem()
     vol = inputs.volume(prob["dims"])
     s_exact = dense.exact_sign(prob["kmat"])
     d = _dense_overlap(s_exact, mu, vol)
@@ -39,7 +48,7 @@ def test_chiral_operator_equals_projected_normal_with_exact_sign(chirality, mu):
 def test_chiral_operator_with_polynomial_sign_within_chebyshev_error(chirality):
     """With the order-64 polynomial sign the identity holds up to the sign's
     own error (S^2 - 1 on the spectrum), measured here directly."""
-    prob = small_problem()
+    prob = _problem()
     mu = 0.05
     cfg = overlap.SignConfig(chebyshev.coefficients(64, prob["a"], prob["b"]), prob["a"], prob["b"],
                              prob["evals"], prob["evecs"])
@@ -55,7 +64,7 @@ def test_chiral_operator_with_polynomial_sign_within_chebyshev_error(chirality):
 
 @pytest.mark.parametrize("chirality", [1, -1])
 def test_chiral_cg_matches_dense_solve(chirality):
-    prob = small_problem()
+    prob = _problem()
     mu = 0.05
     cfg = overlap.SignConfig(chebyshev.coefficients(48, prob["a"], prob["b"]), prob["a"], prob["b"],
                              prob["evals"], prob["evecs"])
@@ -85,7 +94,7 @@ def test_chiral_cg_matches_dense_solve(chirality):
 def test_chiral_coefficient_mistakes_are_caught(monkeypatch):
     """A planted sign error in the chirality term, or (1 - mu) for (1 + mu) in
     the diagonal, makes the exact-sign pin fail."""
-    prob = small_problem()
+    prob = _problem()
     vol = inputs.volume(prob["dims"])
     mu, chirality = 0.3, 1
     s_exact = dense.exact_sign(prob["kmat"])
