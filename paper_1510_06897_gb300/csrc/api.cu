@@ -230,6 +230,8 @@ ov_status ov_get_stats(const ov_ctx* c, ov_stats* out) {
   out->stencil_minb = I.cfg.minb;
   out->stencil_lrec = (I.p == OP_F64) ? 18 : I.cfg.lrec;
   out->stencil_slab = I.cfg.slab;
+  out->stencil_async = I.cfg.async;
+  out->stencil_brick = I.cfg.brick;
   return OV_OK;
 }
 

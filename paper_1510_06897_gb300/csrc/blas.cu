@@ -137,15 +137,14 @@ __global__ void k_pack_links(const double2* __restrict__ in, void* __restrict__ 
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       q[c * V + s] = make_float4((float)u[2 * c].x, (float)u[2 * c].y, (float)u[2 * c + 1].x, (float)u[2 * c + 1].y);
-  } else if constexpr (LREC == 18) {
-    uint2* q = static_cast<uint2*>(out) + (int64_t)mu * 5 * V;
+  } else if constexpr (LREC == 18) {  // entries 0-3, 4-7 as uint4 chunks, entry 8 as one word
+    uint32_t w[9];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      uint2 v;
-      v.x = pack2<T>((float)u[2 * c].x, (float)u[2 * c].y);
-      v.y = (c < 4) ? pack2<T>((float)u[2 * c + 1].x, (float)u[2 * c + 1].y) : 0u;
-      q[c * V + s] = v;
-    }
+    for (int e = 0; e < 9; ++e) w[e] = pack2<T>((float)u[e].x, (float)u[e].y);
+    uint4* q = static_cast<uint4*>(out);
+    q[(int64_t)mu * V + s] = make_uint4(w[0], w[1], w[2], w[3]);
+    q[(int64_t)(4 + mu) * V + s] = make_uint4(w[4], w[5], w[6], w[7]);
+    reinterpret_cast<uint32_t*>(q + (int64_t)8 * V)[(int64_t)mu * V + s] = w[8];
   } else {
     uint2* q = static_cast<uint2*>(out) + (int64_t)mu * 3 * V;
 #pragma unroll

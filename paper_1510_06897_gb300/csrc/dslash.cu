@@ -1,5 +1,7 @@
 // Stencil dispatch: picks the per-precision launcher compiled in
 // dslash_f64.cu / dslash_f32.cu / dslash_f16.cu / dslash_b16.cu.
+#include <cstdlib>
+
 #include "dslash_slab.cuh"
 
 namespace ov {
@@ -21,6 +23,14 @@ int slab_ctas_per_sm(const LatticeH& g) {
     return 0;
   }
   return n;
+}
+
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* env = std::getenv("OV_PDL");
+    return !(env && std::atoi(env) == 0);
+  }();
+  return on;
 }
 
 L2Window& l2_window() {

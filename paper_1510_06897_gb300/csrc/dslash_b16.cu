@@ -1,4 +1,5 @@
 // Stencil instantiations for B16 storage (see dslash_kernel.cuh).
+#include "dslash_async.cuh"
 #include "dslash_slab.cuh"
 
 namespace ov {
@@ -14,6 +15,10 @@ bool launch_dslash_b16(const DslashCfg& c, OpPrec out_prec, const LatticeH& g, c
     const DslashCfg d{};
     if (out_prec == OP_F32) return launch_variant<B16, 12, B16, F32>(d, g, links, in, out, e, nrhs, st);
     return launch_variant<B16, 12, B16, B16>(d, g, links, in, out, e, nrhs, st);
+  }
+  if (c.async > 0) {
+    return (out_prec == OP_F32) ? launch_async<B16, F32>(c, g, links, in, out, e, nrhs, st)
+                                : launch_async<B16, B16>(c, g, links, in, out, e, nrhs, st);
   }
   if (out_prec == OP_F32) {
     if (c.lrec == 18) return launch_variant<B16, 18, B16, F32>(c, g, links, in, out, e, nrhs, st);

@@ -1,4 +1,5 @@
 // Stencil instantiations for F16 storage (see dslash_kernel.cuh).
+#include "dslash_async.cuh"
 #include "dslash_slab.cuh"
 
 namespace ov {
@@ -14,6 +15,10 @@ bool launch_dslash_f16(const DslashCfg& c, OpPrec out_prec, const LatticeH& g, c
     const DslashCfg d{};
     if (out_prec == OP_F32) return launch_variant<F16, 12, F16, F32>(d, g, links, in, out, e, nrhs, st);
     return launch_variant<F16, 12, F16, F16>(d, g, links, in, out, e, nrhs, st);
+  }
+  if (c.async > 0) {
+    return (out_prec == OP_F32) ? launch_async<F16, F32>(c, g, links, in, out, e, nrhs, st)
+                                : launch_async<F16, F16>(c, g, links, in, out, e, nrhs, st);
   }
   if (out_prec == OP_F32) {
     if (c.lrec == 18) return launch_variant<F16, 18, F16, F32>(c, g, links, in, out, e, nrhs, st);

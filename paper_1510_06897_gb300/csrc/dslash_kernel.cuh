@@ -192,25 +192,79 @@ struct Geo {
   int V;
   int LxLy;
   int antiperiodic_t;
+  int brick_z;  // 0: a block covers consecutive sites of one (x, y) plane; > 0: an 8 x 4 x brick_z brick
 };
+
+// Site coordinates of this thread.  Plane mapping: grid x runs over the
+// sites of an (x, y) plane, grid y over the (z, t) slices.  Brick mapping:
+// a block of 32 brick_z threads covers an 8 x 4 x brick_z brick of one t
+// slice (grid x: bricks of the (x, y, z) volume, grid y: t), so that more of
+// the z and y neighbours a block reads are its own sites, whose lines the
+// block's other loads already brought into L1.  Returns false for the
+// padding threads of a plane.
+__device__ __forceinline__ bool site_of_thread(const Geo& g, int& x, int& y, int& z, int& t) {
+  const int Lx = g.L[0], Lz = g.L[2];
+  if (g.brick_z > 0) {
+    const int tid = threadIdx.x;
+    const int nbx = Lx >> 3, nby = g.L[1] >> 2;
+    const int b = blockIdx.x;
+    const int bxi = b % nbx, r = b / nbx;
+    const int byi = r % nby, bzi = r / nby;
+    x = (bxi << 3) + (tid & 7);
+    y = (byi << 2) + ((tid >> 3) & 3);
+    z = bzi * g.brick_z + (tid >> 5);
+    t = blockIdx.y;
+    return true;
+  }
+  const int xy = blockIdx.x * blockDim.x + threadIdx.x;
+  if (xy >= g.LxLy) return false;
+  const int slice = blockIdx.y;
+  y = xy / Lx;
+  x = xy - y * Lx;
+  t = slice / Lz;
+  z = slice - t * Lz;
+  return true;
+}
+
+// Grid of a stencil launch for either mapping (z: right-hand-side tiles).
+inline dim3 stencil_grid(const Geo& g, int tpb, unsigned ztiles) {
+  if (g.brick_z > 0)
+    return dim3((unsigned)((g.L[0] / 8) * (g.L[1] / 4) * (g.L[2] / g.brick_z)), (unsigned)g.L[3], ztiles);
+  return dim3((unsigned)((g.LxLy + tpb - 1) / tpb), (unsigned)(g.L[2] * g.L[3]), ztiles);
+}
+
+
 
 // Grid: x = sites of one (x, y) plane, y = z + Lz t slice, z = tile of RT
 // right-hand sides.  LT/LREC: link storage and 12- or 18-real layout, ST:
 // storage of the stencil input and of v[j], OT: storage of z, y and the
 // output.  MINB: minimum resident blocks of 256 threads requested from the
-// register allocator (1: no cap, 2: <= 128 registers, 3: <= 80, 4: <= 64).
+// register allocator (1: no cap, 2: <= 128 registers, 3: <= 80, 4: <= 64),
+// or (MINB 5) 14 resident blocks of at most 64 threads (<= 72 registers):
+// an occupancy between the 256-thread caps that lets the number of waves of
+// a launch end closer to a whole number (4.87 instead of 4.26 on 24^3 x 48).
+constexpr int lb_threads(int minb) { return minb == 5 ? 64 : 256; }
+constexpr int lb_blocks(int minb) { return minb == 5 ? 14 : minb; }
+// Programmatic dependent launch: a stencil launched with the
+// programmatic-stream-serialisation attribute may start while the previous
+// kernel of the stream drains; it lets its own dependents start likewise and
+// waits for the previous kernel to complete (and its writes to be visible)
+// before its first global access.  Without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
 template <class LT, int LREC, class ST, class OT, int MINB, int RT>
-__global__ void __launch_bounds__(256, MINB) k_dslash(Geo g, const void* __restrict__ links,
+__global__ void __launch_bounds__(lb_threads(MINB), lb_blocks(MINB)) k_dslash(Geo g, const void* __restrict__ links,
                                                       const char* __restrict__ in, char* out, EpiDev<typename Store<ST>::R> e,
                                                       long long rhs_bytes, long long out_rhs_bytes, int nrhs) {
   using R = typename Store<ST>::R;
-  const int xy = blockIdx.x * blockDim.x + threadIdx.x;
-  if (xy >= g.LxLy) return;
-  const int slice = blockIdx.y;
+  pdl_enter();
+  int x, y, z, t;
+  if (!site_of_thread(g, x, y, z, t)) return;
   const int Lx = g.L[0], Ly = g.L[1], Lz = g.L[2], Lt = g.L[3];
-  const int y = xy / Lx, x = xy - y * Lx;
-  const int t = slice / Lz, z = slice - t * Lz;
-  const int s = slice * g.LxLy + xy;
+  const int s = (t * Lz + z) * g.LxLy + y * Lx + x;
   const int V = g.V;
   const int r0 = blockIdx.z * RT;
   const int nv = min(RT, nrhs - r0);
@@ -252,6 +306,7 @@ inline Geo make_geo(const LatticeH& gh) {
   g.V = (int)gh.V;
   g.LxLy = gh.L[0] * gh.L[1];
   g.antiperiodic_t = gh.antiperiodic_t;
+  g.brick_z = 0;
   return g;
 }
 
@@ -283,27 +338,43 @@ inline EpiDev<R> make_epi(const EpiArgs& ea) {
   return e;
 }
 
+// Whether stencil launches overlap the previous kernel's drain (programmatic
+// dependent launch; OV_PDL=0 turns it off).
+bool pdl_enabled();
+
 // Launches kern<<<grid, block, smem, st>>>(args...), with the persisting L2
-// window on the links when one is set for this links pointer.
+// window on the links when one is set for this links pointer, and with
+// programmatic dependent launch when pdl is set (kernels that call
+// pdl_enter() before any global access).
 template <class... KA, class... A>
 void launch_windowed(void (*kern)(KA...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, const void* links,
-                     A&&... args) {
+                     bool pdl, A&&... args) {
   const L2Window& w = l2_window();
-  if (w.base != nullptr && w.base == links) {
+  const bool window = (w.base != nullptr && w.base == links);
+  if (window || pdl) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
-    attr[0].val.accessPolicyWindow.base_ptr = const_cast<void*>(w.base);
-    attr[0].val.accessPolicyWindow.num_bytes = w.bytes;
-    attr[0].val.accessPolicyWindow.hitRatio = 1.0f;
-    attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-    attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cudaLaunchAttribute attr[2];
+    int n = 0;
+    if (window) {
+      attr[n].id = cudaLaunchAttributeAccessPolicyWindow;
+      attr[n].val.accessPolicyWindow.base_ptr = const_cast<void*>(w.base);
+      attr[n].val.accessPolicyWindow.num_bytes = w.bytes;
+      attr[n].val.accessPolicyWindow.hitRatio = 1.0f;
+      attr[n].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+      attr[n].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+      ++n;
+    }
+    if (pdl) {
+      attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[n].val.programmaticStreamSerializationAllowed = 1;
+      ++n;
+    }
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = n;
     cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
     return;
   }
@@ -312,11 +383,12 @@ void launch_windowed(void (*kern)(KA...), dim3 grid, dim3 block, size_t smem, cu
 
 template <class LT, int LREC, class ST, class OT, int MINB, int RT>
 void launch_k(const LatticeH& gh, const void* links, const void* in, void* out, const EpiArgs& ea, int nrhs, int tpb,
-              cudaStream_t st) {
-  const Geo g = make_geo(gh);
+              bool brick, cudaStream_t st) {
+  Geo g = make_geo(gh);
+  if (brick) g.brick_z = tpb / 32;
   const long long rb = (long long)Store<ST>::bytes_per_site * g.V, orb = (long long)Store<OT>::bytes_per_site * g.V;
-  dim3 grid((unsigned)((g.LxLy + tpb - 1) / tpb), (unsigned)(gh.L[2] * gh.L[3]), (unsigned)((nrhs + RT - 1) / RT));
-  launch_windowed(k_dslash<LT, LREC, ST, OT, MINB, RT>, grid, dim3(tpb), 0, st, links, g, links,
+  const dim3 grid = stencil_grid(g, tpb, (unsigned)((nrhs + RT - 1) / RT));
+  launch_windowed(k_dslash<LT, LREC, ST, OT, MINB, RT>, grid, dim3(tpb), 0, st, links, pdl_enabled(), g, links,
                   static_cast<const char*>(in), static_cast<char*>(out), make_epi<typename Store<ST>::R>(ea), rb, orb,
                   nrhs);
 }
@@ -325,12 +397,14 @@ void launch_k(const LatticeH& gh, const void* links, const void* in, void* out, 
 template <class LT, int LREC, class ST, class OT>
 bool launch_variant(const DslashCfg& c, const LatticeH& g, const void* links, const void* in, void* out,
                     const EpiArgs& e, int nrhs, cudaStream_t st) {
+  if (c.brick && !brick_lattice_ok(g, c.tpb)) return false;
 #define OV_V(MB, RTV)                                                                 \
   if (c.minb == MB && c.rt == RTV) {                                                  \
-    launch_k<LT, LREC, ST, OT, MB, RTV>(g, links, in, out, e, nrhs, c.tpb, st);       \
+    launch_k<LT, LREC, ST, OT, MB, RTV>(g, links, in, out, e, nrhs, c.tpb, c.brick != 0, st); \
     return true;                                                                      \
   }
-  OV_V(2, 1) OV_V(3, 1) OV_V(4, 1)
+  if (c.minb >= 5 && c.tpb > 64) return false;  // these caps are compiled for blocks of <= 64 threads
+  OV_V(2, 1) OV_V(3, 1) OV_V(4, 1) OV_V(5, 1)
   if constexpr (!std::is_same<ST, F64>::value) {
     OV_V(2, 2) OV_V(3, 2) OV_V(1, 3) OV_V(2, 3) OV_V(1, 4) OV_V(2, 4) OV_V(1, 6)
   }

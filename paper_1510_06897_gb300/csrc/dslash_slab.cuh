@@ -408,7 +408,7 @@ bool launch_slab(const DslashCfg& c, const LatticeH& gh, const void* links, cons
   const long long rb = (long long)Store<T>::bytes_per_site * g.V, orb = (long long)Store<OT>::bytes_per_site * g.V;
   const long long nitems = (long long)gh.L[2] * gh.L[3] * nrhs;
   const unsigned grid = (unsigned)std::min<long long>(nitems, c.slab);
-  launch_windowed(slab::k_dslash_slab<T, OT>, dim3(grid), dim3(P + 32), smem, st, links, g,
+  launch_windowed(slab::k_dslash_slab<T, OT>, dim3(grid), dim3(P + 32), smem, st, links, false, g,
                   static_cast<const char*>(links), static_cast<const char*>(in), static_cast<char*>(out), se, rb, orb,
                   nrhs, slab::slab_slots(P), static_cast<volatile int*>(c.err));
   return true;

@@ -15,7 +15,7 @@ inline int spinor_bytes_per_site(OpPrec p) {
 }
 // bytes of one direction's link at one site as stored
 inline int link_bytes_per_site_dir(OpPrec p, int lrec = 12) {
-  return p == OP_F64 ? 144 : p == OP_F32 ? 48 : (lrec == 18 ? 40 : 24);
+  return p == OP_F64 ? 144 : p == OP_F32 ? 48 : (lrec == 18 ? 36 : 24);
 }
 
 struct LatticeH {
@@ -55,8 +55,18 @@ struct DslashCfg {
   int lrec = 12;
   int rt = 1;  // right-hand sides per thread (each link loaded once for all of them)
   int slab = 0;  // > 0: the slab kernel (16-bit storage, 12-real links) on this many persistent CTAs
+  int async = 0;  // 16-bit storage, 12-real links, one RHS per thread: 1 = operands staged in shared memory
+                  // by asynchronous copies (spinors and links), 2 = spinors only (dslash_async.cuh)
+  int brick = 0;  // 1: a block covers an 8 x 4 x (tpb / 32) brick of sites (Lx % 8 = Ly % 4 = 0,
+                  // Lz % (tpb / 32) = 0) instead of consecutive sites of an (x, y) plane
   int* err = nullptr;  // slab kernel: set to 1 (device-visible memory) if a bulk copy did not land in time
 };
+
+// Whether blocks of tpb threads can be mapped onto 8 x 4 x (tpb / 32) bricks.
+inline bool brick_lattice_ok(const LatticeH& g, int tpb) {
+  const int bz = tpb / 32;
+  return tpb % 32 == 0 && bz >= 1 && g.L[0] % 8 == 0 && g.L[1] % 4 == 0 && g.L[2] % bz == 0;
+}
 
 // Whether the slab kernel takes this lattice (Lx Ly a multiple of 32, at most 640).
 bool slab_lattice_ok(const LatticeH& g);

@@ -263,22 +263,33 @@ __device__ __forceinline__ void reconstruct16(uint32_t (&uw)[9]) {
   uw[8] = cc(uw[0], n0, uw[4], uw[1], n1, uw[3]);
 }
 
-// The 9 packed words of U_mu(s) for 16-bit links: 12 stored reals (row 2
-// rebuilt by reconstruct16) or all 18: 5 uint2 chunks per direction at
-// [(mu * 5 + c) V + s], chunk c holding entries 2c and 2c + 1 (the second half
-// of chunk 4 unused).
+// The 9 packed words of U_mu(s) for 16-bit links: 12 stored reals, 3 uint2
+// chunks per direction at [(mu * 3 + c) V + s] (row 2 rebuilt by
+// reconstruct16), or all 18 in 36 bytes: entries 0-3 and 4-7 as uint4 chunks
+// at [mu V + s] and [(4 + mu) V + s], entry 8 as a word at [mu V + s] after
+// the 8 V uint4 chunks (every chunk array starts 16-byte aligned).
 template <class T, int LREC>
 __device__ __forceinline__ void load_link_words16(const void* p, int mu, int s, int V, uint32_t (&uw)[9]) {
-  const uint2* q = static_cast<const uint2*>(p) + (int64_t)mu * (LREC == 18 ? 5 : 3) * V;
-#pragma unroll
-  for (int c = 0; c < (LREC == 18 ? 4 : 3); ++c) {
-    const uint2 v = __ldg(q + c * V + s);
-    uw[2 * c] = v.x;
-    uw[2 * c + 1] = v.y;
-  }
   if constexpr (LREC == 18) {
-    uw[8] = __ldg(q + 4 * V + s).x;
+    const uint4* q = static_cast<const uint4*>(p);
+    const uint4 a = __ldg(q + (int64_t)mu * V + s), b = __ldg(q + (int64_t)(4 + mu) * V + s);
+    uw[0] = a.x;
+    uw[1] = a.y;
+    uw[2] = a.z;
+    uw[3] = a.w;
+    uw[4] = b.x;
+    uw[5] = b.y;
+    uw[6] = b.z;
+    uw[7] = b.w;
+    uw[8] = __ldg(reinterpret_cast<const uint32_t*>(q + (int64_t)8 * V) + (int64_t)mu * V + s);
   } else {
+    const uint2* q = static_cast<const uint2*>(p) + (int64_t)mu * 3 * V;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const uint2 v = __ldg(q + c * V + s);
+      uw[2 * c] = v.x;
+      uw[2 * c + 1] = v.y;
+    }
     reconstruct16<T>(uw);
   }
 }

@@ -43,10 +43,15 @@ ov_status time_variant(ov_ctx* c, Inst& I, const DslashCfg& cfg, const void* lin
 }
 
 // (minb, rt) pairs compiled for the stencil (see dslash_kernel.cuh).
-const int kVariants[][2] = {{2, 1}, {3, 1}, {4, 1}, {2, 2}, {3, 2}, {1, 3}, {2, 3}, {1, 4}, {2, 4}, {1, 6}};
+// (minb 5: <= 64-thread blocks, 14 resident; see dslash_kernel.cuh)
+const int kVariants[][2] = {{2, 1}, {3, 1}, {4, 1}, {5, 1}, {2, 2}, {3, 2}, {1, 3}, {2, 3}, {1, 4}, {2, 4}, {1, 6}};
 
-// The environment variable OV_STENCIL="tpb,minb,lrec[,rt]" (e.g. "192,3,12")
-// skips the timing and pins one variant (used for reproducible profiles);
+// The environment variable OV_STENCIL="tpb,minb,lrec[,rt[,async[,brick]]]"
+// (e.g. "192,3,12" or "64,4,12,1,1") skips the timing and pins one variant
+// (used for reproducible profiles; async 1 / 2 selects the shared-memory
+// staged kernel for 16-bit storage, register cap minb 3 or 4, 12-real links,
+// rt 1; brick 1 maps blocks onto 8 x 4 x (tpb / 32) bricks of sites where the
+// lattice allows it);
 // OV_STENCIL="slab" pins the slab kernel where it applies (16-bit storage,
 // Lx Ly a multiple of 32 up to 640), the default gather variant elsewhere.
 bool pinned_cfg(DslashCfg* cfg, bool* bad) {
@@ -58,16 +63,20 @@ bool pinned_cfg(DslashCfg* cfg, bool* bad) {
     cfg->slab = 1;  // resolved by the caller
     return true;
   }
-  int tpb = 0, minb = 0, lrec = 0, rt = 1;
-  const int n = std::sscanf(env, "%d,%d,%d,%d", &tpb, &minb, &lrec, &rt);
-  bool ok = n >= 3 && tpb >= 32 && tpb <= 256 && tpb % 32 == 0 && (lrec == 12 || lrec == 18);
+  int tpb = 0, minb = 0, lrec = 0, rt = 1, as = 0, bk = 0;
+  const int n = std::sscanf(env, "%d,%d,%d,%d,%d,%d", &tpb, &minb, &lrec, &rt, &as, &bk);
+  bool ok = n >= 3 && tpb >= 32 && tpb <= 256 && tpb % 32 == 0 && (lrec == 12 || lrec == 18) && as >= 0 && as <= 2 &&
+            (bk == 0 || bk == 1) && !(minb >= 5 && tpb > 64);
   bool listed = false;
   for (const auto& v : kVariants) listed = listed || (v[0] == minb && v[1] == rt);
+  if (as > 0) listed = (minb == 3 || minb == 4) && rt == 1 && lrec == 12;
   if (!ok || !listed) {
     *bad = true;
     return false;
   }
   *cfg = DslashCfg{tpb, minb, lrec, rt};
+  cfg->async = as;
+  cfg->brick = bk;
   return true;
 }
 
@@ -113,6 +122,8 @@ ov_status autotune(ov_ctx* c, Inst& I, const void* links_dev) {
   } else if (pinned) {
     best_cfg = DslashCfg{pin.tpb, pin.minb, is16 ? pin.lrec : 12, 1};
     if (I.p == OP_F64 && pin.rt != 1) best_cfg.rt = 1;
+    if (is16) best_cfg.async = pin.async;  // the staged kernel exists for 16-bit storage only
+    best_cfg.brick = (pin.brick && brick_lattice_ok(c->g, pin.tpb)) ? 1 : 0;
   } else if (V >= 4096) {
     DevBuf buf[4];
     for (DevBuf& b : buf) {
@@ -132,13 +143,29 @@ ov_status autotune(ov_ctx* c, Inst& I, const void* links_dev) {
       if (!is16 && lrec == 18) continue;
       const void* links = (lrec == 18 && is16) ? alt.p : I.links.p;
       for (int tpb : {64, 96, 128, 192, 256})
-        for (const auto& v : kVariants) {
-          if (v[1] != 1) continue;
-          DslashCfg cfg{tpb, v[0], is16 ? lrec : 12, 1};
-          float ms = 0.f;
-          OV_TRY(time_variant(c, I, cfg, links, 1, buf, e0, e1, &ms));
-          cands.push_back({ms, cfg, links});
-        }
+        for (const auto& v : kVariants)
+          for (int bk : {0, 1}) {
+            if (v[1] != 1 || (bk && !brick_lattice_ok(c->g, tpb)) || (v[0] >= 5 && tpb > 64)) continue;
+            DslashCfg cfg{tpb, v[0], is16 ? lrec : 12, 1};
+            cfg.brick = bk;
+            float ms = 0.f;
+            OV_TRY(time_variant(c, I, cfg, links, 1, buf, e0, e1, &ms));
+            cands.push_back({ms, cfg, links});
+          }
+    }
+    if (is16) {  // the shared-memory staged kernel (12-real links)
+      for (int tpb : {64, 96, 128, 192, 256})
+        for (int minb : {3, 4})
+          for (int as : {1, 2})
+            for (int bk : {0, 1}) {
+              if (bk && !brick_lattice_ok(c->g, tpb)) continue;
+              DslashCfg cfg{tpb, minb, 12, 1};
+              cfg.async = as;
+              cfg.brick = bk;
+              float ms = 0.f;
+              OV_TRY(time_variant(c, I, cfg, I.links.p, 1, buf, e0, e1, &ms));
+              cands.push_back({ms, cfg, I.links.p});
+            }
     }
     DslashCfg sc;
     if (slab_cfg(c, I, &sc)) {
@@ -190,6 +217,8 @@ ov_status batch_cfg(ov_ctx* c, Inst& I, int nrhs, DslashCfg* out) {
     if (!pin.slab) {
       best_cfg = DslashCfg{pin.tpb, pin.minb, I.cfg.lrec, (I.p == OP_F64) ? 1 : pin.rt};
       if (best_cfg.rt == 1 && best_cfg.minb == 1) best_cfg.minb = 2;
+      if ((I.p == OP_F16 || I.p == OP_B16) && I.cfg.lrec == 12) best_cfg.async = pin.async;
+      best_cfg.brick = (pin.brick && brick_lattice_ok(c->g, pin.tpb)) ? 1 : 0;
     }
   } else if (c->g.V >= 4096) {
     const int64_t V = c->g.V;
@@ -203,16 +232,37 @@ ov_status batch_cfg(ov_ctx* c, Inst& I, int nrhs, DslashCfg* out) {
     OV_CK(cudaEventCreate(&e1));
     float best = 1e30f;
     for (int tpb : {64, 96, 128, 192, 256})
-      for (const auto& v : kVariants) {
-        if (v[1] > nrhs || (I.p == OP_F64 && v[1] != 1)) continue;
-        DslashCfg cfg{tpb, v[0], I.cfg.lrec, v[1]};
-        float ms = 0.f;
-        OV_TRY(time_variant(c, I, cfg, I.links.p, nrhs, buf, e0, e1, &ms));
-        if (ms < best) {
-          best = ms;
-          best_cfg = cfg;
+      for (const auto& v : kVariants)
+        for (int bk : {0, 1}) {
+          if (v[1] > nrhs || (I.p == OP_F64 && v[1] != 1) || (bk && !brick_lattice_ok(c->g, tpb)) ||
+              (v[0] >= 5 && tpb > 64))
+            continue;
+          DslashCfg cfg{tpb, v[0], I.cfg.lrec, v[1]};
+          cfg.brick = bk;
+          float ms = 0.f;
+          OV_TRY(time_variant(c, I, cfg, I.links.p, nrhs, buf, e0, e1, &ms));
+          if (ms < best) {
+            best = ms;
+            best_cfg = cfg;
+          }
         }
-      }
+    if ((I.p == OP_F16 || I.p == OP_B16) && I.cfg.lrec == 12) {  // the staged kernel, one RHS per thread
+      for (int tpb : {64, 96, 128, 192, 256})
+        for (int minb : {3, 4})
+          for (int as : {1, 2})
+            for (int bk : {0, 1}) {
+              if (bk && !brick_lattice_ok(c->g, tpb)) continue;
+              DslashCfg cfg{tpb, minb, 12, 1};
+              cfg.async = as;
+              cfg.brick = bk;
+              float ms = 0.f;
+              OV_TRY(time_variant(c, I, cfg, I.links.p, nrhs, buf, e0, e1, &ms));
+              if (ms < best) {
+                best = ms;
+                best_cfg = cfg;
+              }
+            }
+    }
     DslashCfg sc;
     if (I.cfg.lrec == 12 && slab_cfg(c, I, &sc)) {
       float ms = 0.f;

@@ -15,8 +15,8 @@ from tests.oracle_fixtures import field_shape, small_problem
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [(128, 2, 1), (192, 3, 1), (256, 4, 1), (128, 2, 2), (192, 3, 2), (96, 1, 3), (128, 2, 3), (64, 1, 4),
-            (256, 2, 4), (64, 1, 6)]
+VARIANTS = [(128, 2, 1), (192, 3, 1), (256, 4, 1), (64, 5, 1), (128, 2, 2), (192, 3, 2), (96, 1, 3), (128, 2, 3),
+            (64, 1, 4), (256, 2, 4), (64, 1, 6)]
 TOL = {"fp64": 1e-13, "fp32": 1e-6, "fp16": 2e-3, "bf16": 1.5e-2}
 
 
@@ -47,6 +47,89 @@ def test_stencil_variants(pin, prec, variant):
         assert c.stats()["stencil_tpb"] == tpb
     want = np.stack([wilson.kernel_k(links, p, antiperiodic_t=True) for p in psi])
     assert rel(got, want) < TOL[prec]
+
+
+ASYNC_VARIANTS = [(64, 4, 1), (64, 3, 2), (96, 3, 1), (128, 4, 2), (256, 3, 1)]
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("variant", ASYNC_VARIANTS)
+def test_staged_stencil_variants(monkeypatch, prec, variant):
+    """The shared-memory staged kernel (asynchronous copies, spinors and links or
+    spinors only) pinned: D_W and K on a ragged plane (48 sites against 64- to
+    256-thread blocks) with an antiperiodic t boundary, against the oracle and
+    bit for bit against the gather kernel, which does the same arithmetic in
+    the same order."""
+    tpb, minb, staged = variant
+    dims = (8, 6, 4, 10)
+    links = inputs.gauge_links(dims, seed=8031)
+    psi = inputs.gaussian_source(dims, seed=8032, nrhs=3)
+    results = {}
+    for name, pin in (("gather", f"{tpb},{minb},12,1"), ("staged", f"{tpb},{minb},12,1,{staged}")):
+        monkeypatch.setenv("OV_STENCIL", pin)
+        with Ctx(dims, dev(links), prec, antiperiodic_t=True) as c:
+            assert c.stats()["stencil_async"] == (staged if name == "staged" else 0)
+            results[name] = (c.wilson(dev(psi)), c.kernel(dev(psi)))
+    assert torch.equal(results["gather"][0], results["staged"][0])
+    assert torch.equal(results["gather"][1], results["staged"][1])
+    want_w = np.stack([wilson.wilson(links, p, True) for p in psi])
+    want_k = np.stack([wilson.kernel_k(links, p, antiperiodic_t=True) for p in psi])
+    assert rel(host(results["staged"][0]), want_w) < TOL[prec]
+    assert rel(host(results["staged"][1]), want_k) < TOL[prec]
+
+
+BRICK_VARIANTS = [("64,4,{l},1,0", "fp16"), ("96,3,{l},1,0", "fp32"), ("192,3,{l},2,0", "bf16"), ("64,3,12,1,1", "fp16"),
+                  ("128,4,12,1,2", "bf16"), ("64,4,12,1,0", "fp64"), ("128,2,{l},3,0", "fp16")]
+
+
+@pytest.mark.parametrize("pin,prec", BRICK_VARIANTS)
+def test_brick_mapping(monkeypatch, pin, prec):
+    """Blocks mapped onto 8 x 4 x (tpb / 32) bricks of sites (8 x 4 x 12 x 6
+    lattice: 2 to 6 brick layers in z, antiperiodic t): D_W and K against the
+    oracle and bit for bit against the plane mapping of the same variant."""
+    lrec = 18 if prec == "bf16" else 12
+    pin = pin.format(l=lrec)
+    dims = (8, 4, 12, 6)
+    links = inputs.gauge_links(dims, seed=8051)
+    psi = inputs.gaussian_source(dims, seed=8052, nrhs=3)
+    res = {}
+    for bk in (0, 1):
+        monkeypatch.setenv("OV_STENCIL", f"{pin},{bk}")
+        with Ctx(dims, dev(links), prec, antiperiodic_t=True) as c:
+            assert c.stats()["stencil_brick"] == bk
+            res[bk] = (c.wilson(dev(psi)), c.kernel(dev(psi)))
+    assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])
+    want_w = np.stack([wilson.wilson(links, p, True) for p in psi])
+    want_k = np.stack([wilson.kernel_k(links, p, antiperiodic_t=True) for p in psi])
+    assert rel(host(res[1][0]), want_w) < TOL[prec]
+    assert rel(host(res[1][1]), want_k) < TOL[prec]
+
+
+@pytest.mark.parametrize("staged", [1, 2])
+def test_staged_sign_and_overlap(monkeypatch, staged):
+    """sign(K), D[mu] and D[mu]^dagger through the staged kernel: every
+    epilogue form of the recurrence (three staged vectors), the deflation
+    correction and the FP32 assembly, 8 deflated pairs at 4^4, order 24, FP16;
+    bit for bit against the gather kernel and within the FP16 bound of the
+    oracle."""
+    prob = small_problem()
+    psi = inputs.gaussian_source(prob["dims"], seed=8041, nrhs=2)
+    order, mu = 24, 0.1
+    cfg = overlap.SignConfig(chebyshev.coefficients(order, prob["a"], prob["b"]), prob["a"], prob["b"],
+                             prob["evals"], prob["evecs"])
+    out = {}
+    for name, pin in (("gather", "64,4,12,1"), ("staged", f"64,4,12,1,{staged}")):
+        monkeypatch.setenv("OV_STENCIL", pin)
+        with Ctx(prob["dims"], dev(prob["links"]), "fp16") as c:
+            c.sign_config(order, prob["a"], prob["b"], prob["evals"], dev(prob["evecs"]))
+            out[name] = (c.sign(dev(psi)), c.overlap(dev(psi), mu), c.overlap(dev(psi), mu, dagger=True))
+    for g, s in zip(out["gather"], out["staged"]):
+        assert torch.equal(g, s)
+    want = [np.stack([overlap.sign_apply(prob["links"], p, cfg) for p in psi]),
+            np.stack([overlap.overlap(prob["links"], p, mu, cfg) for p in psi]),
+            np.stack([overlap.overlap_dag(prob["links"], p, mu, cfg) for p in psi])]
+    for got, w in zip(out["staged"], want):
+        assert rel(host(got), w) < 1e-2
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
