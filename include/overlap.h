@@ -84,7 +84,8 @@ typedef struct {
   long long dslash_timed;      /* stencil launches timed while profiling was on */
   double dslash_ms;            /* their summed device time (CUDA events on the context stream) */
   int stencil_tpb;             /* autotuned stencil launch of the context-precision operator: */
-  int stencil_minb;            /*   threads per block, register cap (2/3/4 = 128/85/64 regs), */
+  int stencil_minb;            /*   threads per block, register cap (2/3/4 = 128/80/64 regs; 5 = 72 regs,
+                                      blocks of <= 64 threads), */
   int stencil_lrec;            /*   stored reals per link (12: row 2 rebuilt, 18: all) */
   int tc_gemm_launches;        /* deflation projections run on the tensor cores (several RHS, FP32 vectors) */
   int stencil_slab;            /* > 0: the tuned stencil is the slab kernel on this many persistent CTAs
@@ -92,6 +93,11 @@ typedef struct {
   long long gcr_iterations;    /* GCR steps of the last ov_solve_gmresr (inner_iterations: its SUMR
                                   iterations) */
   int gmresr_order;            /* Chebyshev order of the relaxed sign in that solve */
+  int stencil_async;           /* 1 / 2: the tuned stencil stages each direction's neighbour spinors and
+                                  links (1) or spinors only (2) in shared memory with asynchronous
+                                  copies, double-buffered; 0: loads straight into registers */
+  int stencil_brick;           /* 1: its blocks cover 8 x 4 x (stencil_tpb / 32) bricks of sites;
+                                  0: consecutive sites of one (x, y) plane */
 } ov_stats;
 
 /* Creates a context for one lattice and gauge field (Eq. 2 links).  Copies and
@@ -104,7 +110,7 @@ typedef struct {
  * OV_ERR_NOMEM, OV_ERR_CUDA.
  * The stencil's launch shape and (16-bit) link layout are autotuned here by
  * timing a few launches of each variant on this lattice; the environment
- * variable OV_STENCIL="tpb,minb,lrec" pins one gather variant, OV_STENCIL="slab"
+ * variable OV_STENCIL="tpb,minb,lrec[,rt[,async[,brick]]]" pins one gather variant, OV_STENCIL="slab"
  * the slab kernel where it applies (see ov_stats).
  * For 16-bit precisions the links are marked persisting in L2 for the stencil
  * launches (a per-process limit set here and released by ov_destroy;
@@ -249,6 +255,19 @@ ov_status ov_set_gmresr_params(ov_ctx* ctx, int inner_order, double inner_tol, i
 ov_status ov_eigs(ov_ctx* ctx, int n_ev, double tol, int max_iter, double* evals, void* evecs,
                   double* lambda_max_out);
 
+/* The quadratic form S = chi^dagger P(K) chi, P(K) = K f_N(K^2) the
+ * undeflated polynomial of Eq. 3 on [lo^2, hi^2] (the same order and interval
+ * as ov_sign_poly_grad; the context's sign configuration is neither needed nor
+ * changed).  chi: one spinor in `dtype` (host or device).  *s_out (host)
+ * receives S (real: P(K) is Hermitian), summed in FP64.  p_chi (may be NULL):
+ * receives P(K) chi in `dtype`, whose double is the derivative of S with
+ * respect to chi.  Runs the Clenshaw recurrence of Eq. 3 (2N + 2 stencil
+ * launches) and one FP64 inner product.  Errors: OV_ERR_INVALID (null chi or
+ * s_out, order < 1, not 0 < lo < hi, a context that is neither OV_FP64 nor
+ * OV_FP32), OV_ERR_NOMEM, OV_ERR_CUDA. */
+ov_status ov_sign_poly_quad(ov_ctx* ctx, int order, double lo, double hi, const void* chi, void* p_chi,
+                            ov_dtype dtype, double* s_out);
+
 /* Gradient of S = chi^dagger P(K) chi, P(K) = K f_N(K^2) the undeflated
  * polynomial of Eq. 3 on [lo^2, hi^2], with respect to every link:
  * grad_links complex128 [4][V][3][3] receives F_mu(x) in su(3) with
@@ -288,8 +307,9 @@ ov_status ov_get_residual_history(const ov_ctx* ctx, double* out, int max_len, i
 ov_status ov_get_stats(const ov_ctx* ctx, ov_stats* out);
 ov_status ov_reset_stats(ov_ctx* ctx);
 
-/* No counterpart in the paper.  D_W in (Eq. 2 operator, FP64 arithmetic, as
- * ov_wilson on an OV_FP64 context) for callers that cannot allocate device
+/* No counterpart in the paper.  D_W in (the Wilson operator of ov_wilson, FP64
+ * arithmetic, the result of ov_wilson on an OV_FP64 context; D_W itself has no
+ * m_W, which enters only K) for callers that cannot allocate device
  * memory at all: code embedded in a framework whose memory pool owns the
  * whole GPU, or a latency-critical loop where a cudaMalloc may block or fail.
  * No context is needed and nothing is allocated: the packed copies of links
@@ -297,7 +317,9 @@ ov_status ov_reset_stats(ov_ctx* ctx);
  * GPU that loads this library until the process exits.  Requirements:
  * V * (576 + 384 * nrhs) <= 32 MiB (e.g. V <= 34952 sites for one RHS), else
  * OV_ERR_INVALID; links (complex128 [4][V][3][3]), in and out (dtype
- * [nrhs][V][4][3]) in device memory, else OV_ERR_INVALID.  Work is issued on
+ * [nrhs][V][4][3]) in device memory of the current device, else
+ * OV_ERR_INVALID (the sizes of these buffers cannot be checked here: out and
+ * in must hold nrhs * 12 * V elements of dtype).  Work is issued on
  * cuda_stream (NULL = legacy default stream) and the call returns when it is
  * complete.  All calls share the array, which keeps the last call's contents
  * (each call writes everything it reads, so nothing needs clearing): calls

@@ -47,7 +47,9 @@ class ov_stats(ctypes.Structure):
                 ("tc_gemm_launches", ctypes.c_int),
                 ("stencil_slab", ctypes.c_int),
                 ("gcr_iterations", ctypes.c_longlong),
-                ("gmresr_order", ctypes.c_int)]
+                ("gmresr_order", ctypes.c_int),
+                ("stencil_async", ctypes.c_int),
+                ("stencil_brick", ctypes.c_int)]
 
 
 _LIB = None
@@ -78,6 +80,7 @@ _SIGNATURES = {
     "ov_set_profiling": [_vp, _i],
     "ov_set_checks": [_vp, _i],
     "ov_get_residual_history": [_vp, ctypes.POINTER(_d), _i, ctypes.POINTER(_i)],
+    "ov_sign_poly_quad": [_vp, _i, _d, _d, _vp, _vp, _i, ctypes.POINTER(_d)],
     "ov_wilson_noalloc": [ctypes.POINTER(_i), _vp, _vp, _vp, _i, _i, _i, _vp],
     "ov_stout_smear": [ctypes.POINTER(_i), _vp, _vp, _d, _d, _i, _vp],
 }
@@ -254,6 +257,14 @@ def ov_eigs(ctx, n_ev, tol, max_iter, evecs, allow_not_converged=False):
     return evals, lmax.value
 
 
+def ov_sign_poly_quad(ctx, order, lo, hi, chi, p_chi=None):
+    """S = chi^dagger P(K) chi (undeflated polynomial); p_chi, if given, receives P(K) chi."""
+    s = _d(0.0)
+    _check(lib().ov_sign_poly_quad(ctx, int(order), float(lo), float(hi), _ptr(chi), _ptr(p_chi), _dtype_code(chi),
+                                   ctypes.byref(s)), ctx)
+    return s.value
+
+
 def ov_sign_poly_grad(ctx, order, lo, hi, chi, grad_links):
     return _check(lib().ov_sign_poly_grad(ctx, int(order), float(lo), float(hi), _ptr(chi), _ptr(grad_links),
                                           _dtype_code(chi)), ctx)
@@ -265,8 +276,24 @@ def ov_get_stats(ctx):
     return {name: getattr(s, name) for name, _ in ov_stats._fields_}
 
 
+def _numel(x):
+    return int(x.size) if isinstance(x, np.ndarray) else int(x.numel())
+
+
 def ov_wilson_noalloc(dims, links, inp, out, nrhs, antiperiodic_t=False, stream=None):
-    """D_W without a context and without any device allocation (see overlap.h)."""
+    """D_W without a context and without any device allocation (see overlap.h).
+    The library cannot see buffer sizes, so they are checked here: links
+    complex128 with 36 V elements, inp 12 V nrhs elements, out the dtype and
+    element count of inp."""
+    vol = 1
+    for d in dims:
+        vol *= int(d)
+    if not str(links.dtype).endswith("complex128") or _numel(links) != 36 * vol:
+        raise ValueError(f"links must be complex128 with 36 * V = {36 * vol} elements")
+    if _numel(inp) != 12 * vol * int(nrhs):
+        raise ValueError(f"inp must hold 12 * V * nrhs = {12 * vol * int(nrhs)} elements")
+    if str(out.dtype) != str(inp.dtype) or _numel(out) != _numel(inp):
+        raise ValueError("out must have the dtype and element count of inp")
     cdims = (_i * 4)(*[int(d) for d in dims])
     return _check(lib().ov_wilson_noalloc(cdims, _ptr(links), _ptr(inp), _ptr(out), int(nrhs), _dtype_code(inp),
                                           int(bool(antiperiodic_t)), _stream_ptr(stream)), None)

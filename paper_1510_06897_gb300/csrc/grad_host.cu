@@ -20,17 +20,104 @@ using namespace ov;
 
 namespace {
 constexpr int kSeg = 16;
+
+// Forward Clenshaw sweep b_k = c_k chi + 2 Z b_{k+1} - b_{k+2}, k = N .. 0
+// (b_{N+1} = b_{N+2} = 0), Z = alpha K^2 + beta: b_k lands in rot[k % 3],
+// t receives K b_{k+1}, and keep(k, b_k) sees every b_k as it is made.
+// Returns b_0 and b_2 (b_2 = zero when N < 2).
+template <class Keep>
+ov_status clenshaw_forward(ov_ctx* c, Inst& I, const std::vector<double>& cf, double alpha, double beta,
+                           const void* xchi, const void* zero, void* const rot[3], void* t, void** b0, const void** b2,
+                           Keep&& keep) {
+  const int N = (int)cf.size() - 1;
+  EpiArgs ek;
+  ek.m_w = c->m_w;
+  const void* bk1 = zero;  // b_{k+1}
+  const void* bk2 = zero;  // b_{k+2}
+  *b2 = zero;
+  for (int k = N; k >= 0; --k) {
+    void* out = rot[k % 3];
+    OV_TRY(k_step(c, I, bk1, t, 1, ek));
+    EpiArgs e;
+    e.m_w = c->m_w;
+    e.s1 = 2.0 * alpha;
+    e.v[0] = bk1;
+    e.w[0] = 2.0 * beta;
+    e.v[1] = bk2;
+    e.w[1] = -1.0;
+    e.v[2] = xchi;
+    e.w[2] = cf[k];
+    OV_TRY(k_step(c, I, t, out, 1, e));
+    OV_TRY(keep(k, out));
+    if (k == 2) *b2 = out;
+    if (k == 0) *b0 = out;
+    bk2 = bk1;
+    bk1 = out;
+  }
+  return OV_OK;
+}
+
+// Arguments shared by ov_sign_poly_quad and ov_sign_poly_grad.
+ov_status check_poly_args(ov_ctx* c, int order, double lo, double hi, const void* chi, const void* out,
+                          ov_dtype dt, const char* name) {
+  if (!chi || !out) return fail(c, OV_ERR_INVALID, "null argument");
+  if (order < 1) return fail(c, OV_ERR_INVALID, "Chebyshev order must be >= 1");
+  if (!(lo > 0.0) || !(hi > lo) || !std::isfinite(hi)) return fail(c, OV_ERR_INVALID, "need 0 < lo < hi");
+  OV_TRY(check_dtype(c, 1, dt));
+  if (c->prec != OV_FP64 && c->prec != OV_FP32)
+    return fail(c, OV_ERR_INVALID, std::string(name) + " needs an OV_FP64 or OV_FP32 context");
+  return OV_OK;
+}
+}  // namespace
+
+// S = chi^dagger P(K) chi = (K chi)^dagger f_N(Z) chi, and optionally P(K) chi.
+extern "C" ov_status ov_sign_poly_quad(ov_ctx* c, int order, double lo, double hi, const void* chi, void* p_chi,
+                                       ov_dtype dt, double* s_out) {
+  if (!c) return OV_ERR_INVALID;
+  OV_TRY(check_poly_args(c, order, lo, hi, chi, s_out, dt, "ov_sign_poly_quad"));
+  Inst& I = (c->prec == OV_FP64) ? c->hi : c->lo;
+  const OpPrec P = I.p;  // == I.pv
+  const int64_t V = c->g.V;
+  const size_t vb = I.vbytes(V);
+  const std::vector<double> cf = chebyshev_coefficients(order, lo, hi);
+  const double a2 = lo * lo, b2 = hi * hi;
+  const double alpha = 2.0 / (b2 - a2), beta = -(b2 + a2) / (b2 - a2);
+  DevBuf xchi, rot3, t, zero, gvec, gbar;
+  OV_CK(xchi.ensure(vb));
+  OV_CK(rot3.ensure(3 * vb));
+  OV_CK(t.ensure(vb));
+  OV_CK(zero.ensure(vb));
+  OV_CK(gvec.ensure(vb));
+  OV_CK(gbar.ensure(vb));
+  OV_CK(c->d_partial.ensure(sizeof(double2) * kReduceBlocks));
+  OV_CK(cudaMemsetAsync(zero.p, 0, vb, c->st));
+  OV_TRY(pack_input(c, I, chi, 1, dt, xchi.p));
+  void* rot[3] = {rot3.c(), rot3.c() + vb, rot3.c() + 2 * vb};
+  void* b0 = nullptr;
+  const void* b2v = nullptr;
+  OV_TRY(clenshaw_forward(c, I, cf, alpha, beta, xchi.p, zero.p, rot, t.p, &b0, &b2v,
+                          [](int, void*) { return OV_OK; }));
+  launch_axpby(P, 0.5, b0, -0.5, b2v, gvec.p, V, 1, c->st);  // f_N(Z) chi = (b_0 - b_2)/2
+  OV_TRY(launched(c));
+  EpiArgs ek;
+  ek.m_w = c->m_w;
+  OV_TRY(k_step(c, I, xchi.p, gbar.p, 1, ek));  // K chi
+  double2 s;
+  OV_TRY(dots(c, P, gbar.p, gvec.p, V, &s));
+  *s_out = s.x;
+  if (p_chi != nullptr) {
+    OV_TRY(k_step(c, I, gvec.p, t.p, 1, ek));  // P(K) chi = K f_N(Z) chi
+    OV_TRY(unpack_output(c, I, t.p, p_chi, 1, dt));
+  }
+  OV_CK(cudaStreamSynchronize(c->st));
+  for (DevBuf* b : {&xchi, &rot3, &t, &zero, &gvec, &gbar}) b->release();
+  return OV_OK;
 }
 
 extern "C" ov_status ov_sign_poly_grad(ov_ctx* c, int order, double lo, double hi, const void* chi,
                                        void* grad_links, ov_dtype dt) {
   if (!c) return OV_ERR_INVALID;
-  if (!chi || !grad_links) return fail(c, OV_ERR_INVALID, "null argument");
-  if (order < 1) return fail(c, OV_ERR_INVALID, "Chebyshev order must be >= 1");
-  if (!(lo > 0.0) || !(hi > lo) || !std::isfinite(hi)) return fail(c, OV_ERR_INVALID, "need 0 < lo < hi");
-  OV_TRY(check_dtype(c, 1, dt));
-  if (c->prec != OV_FP64 && c->prec != OV_FP32)
-    return fail(c, OV_ERR_INVALID, "ov_sign_poly_grad needs an OV_FP64 or OV_FP32 context");
+  OV_TRY(check_poly_args(c, order, lo, hi, chi, grad_links, dt, "ov_sign_poly_grad"));
   Inst& I = (c->prec == OV_FP64) ? c->hi : c->lo;
   const OpPrec P = I.p;  // == I.pv
   const int64_t V = c->g.V;
@@ -85,21 +172,14 @@ extern "C" ov_status ov_sign_poly_grad(ov_ctx* c, int order, double lo, double h
 
   // ---- forward sweep: b_k for k = N .. 0, rotating through three vectors
   void* rot[3] = {slot(segb, 0), slot(segb, 1), slot(segb, 2)};
-  const void* bk1 = zero.p;  // b_{k+1}
-  const void* bk2 = zero.p;  // b_{k+2}
   void* b0 = nullptr;
-  void* b2v = nullptr;
-  for (int k = N; k >= 0; --k) {
-    void* out = rot[k % 3];
-    OV_TRY(clenshaw(k, bk1, bk2, t.p, out));
-    if (void* cs = (k >= 1) ? ck_slot(k) : nullptr) {
-      OV_CK(cudaMemcpyAsync(cs, out, vb, cudaMemcpyDeviceToDevice, c->st));
-    }
-    if (k == 2) b2v = out;
-    if (k == 0) b0 = out;
-    bk2 = bk1;
-    bk1 = out;
-  }
+  const void* b2v = nullptr;
+  OV_TRY(clenshaw_forward(c, I, cf, alpha, beta, xchi.p, zero.p, rot, t.p, &b0, &b2v,
+                          [&](int k, void* bk) -> ov_status {
+                            if (void* cs = (k >= 1) ? ck_slot(k) : nullptr)
+                              OV_CK(cudaMemcpyAsync(cs, bk, vb, cudaMemcpyDeviceToDevice, c->st));
+                            return OV_OK;
+                          }));
   // g = (b_0 - b_2)/2 ; gbar = K chi
   launch_axpby(P, 0.5, b0, -0.5, b2v, gvec.p, V, 1, c->st);
   OV_TRY(launched(c));

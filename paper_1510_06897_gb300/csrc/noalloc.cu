@@ -69,13 +69,17 @@ ov_status scratch_address(void** out) {
   return OV_OK;
 }
 
-bool on_device(const void* p) {
+// Device (or managed) memory that the current device can use: a device
+// pointer of another GPU is refused, since the kernels would run on the
+// current device against memory it may not be able to reach.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
@@ -99,8 +103,11 @@ extern "C" ov_status ov_wilson_noalloc(const int dims[4], const void* links, con
   if (V > (1LL << 27) || link_bytes + 2 * vec_bytes > kNoallocScratchBytes)
     return noalloc_fail(OV_ERR_INVALID, "lattice x nrhs too large for the 32 MiB scratch of ov_wilson_noalloc: needs " +
                                             std::to_string(link_bytes + 2 * vec_bytes) + " bytes");
-  if (!on_device(links) || !on_device(in) || !on_device(out))
-    return noalloc_fail(OV_ERR_INVALID, "links, in and out must be device memory");
+  int cur = 0;
+  const cudaError_t de = cudaGetDevice(&cur);
+  if (de != cudaSuccess) return noalloc_fail(OV_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(de));
+  if (!on_device(links, cur) || !on_device(in, cur) || !on_device(out, cur))
+    return noalloc_fail(OV_ERR_INVALID, "links, in and out must be device memory of the current device");
   void* base = nullptr;
   ov_status s = scratch_address(&base);
   if (s != OV_OK) return s;

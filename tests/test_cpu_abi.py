@@ -151,3 +151,25 @@ def test_stats_struct_matches_the_header():
     fields = re.findall(r"(long long|double|int)\s+([a-z_0-9]+)\s*;", body)
     ctypes_of = {"long long": ctypes.c_longlong, "double": ctypes.c_double, "int": ctypes.c_int}
     assert [(n, ctypes_of[t]) for t, n in fields] == list(binding.ov_stats._fields_)
+
+
+def test_noalloc_binding_checks_buffer_sizes():
+    """The C entry point cannot see buffer sizes; the binding refuses links,
+    inputs and outputs whose dtype or element count does not fit the lattice
+    before anything reaches the library."""
+    dims = (4, 4, 4, 4)
+    vol = 256
+    links = np.zeros((4, 4, 4, 4, 4, 3, 3), dtype=np.complex128)
+    psi = np.zeros((1, 4, 4, 4, 4, 4, 3), dtype=np.complex128)
+    bad = [
+        (links.astype(np.complex64), psi, psi.copy()),           # links in the wrong dtype
+        (links[:3], psi, psi.copy()),                              # links too small
+        (links, psi[:, :3], psi[:, :3].copy()),                    # input too small
+        (links, psi, np.zeros_like(psi, dtype=np.complex64)),      # output dtype differs
+        (links, psi, np.zeros(12 * vol - 1, dtype=np.complex128)),  # output too small
+    ]
+    for lk, x, out in bad:
+        with pytest.raises(ValueError):
+            binding.ov_wilson_noalloc(dims, lk, x, out, 1)
+    with pytest.raises(ValueError):
+        binding.ov_wilson_noalloc(dims, links, psi, psi.copy(), 2)  # nrhs larger than the input

@@ -2,8 +2,13 @@
 example code living inside a framework whose memory pool owns the whole GPU).
 It keeps its packed copies in one fixed device array of the library instead
 of allocating, and must give the same result as ov_wilson on an FP64
-context.  Two calls in a row with different inputs check that nothing left in
-the shared array from the previous call leaks into the next result."""
+context.
+
+No test here depends on the others: the file is named to be collected last
+only so that, should it fail, a run stopped at the first failure has already
+run every other test.  Each case works on its own inputs and its own
+contexts, and it passes alone in a fresh process as well as after the rest.
+"""
 import numpy as np
 import pytest
 
@@ -22,8 +27,8 @@ def _gpu():
     need_gpu()
 
 
-def _reference(dims, links, psi, antiperiodic):
-    with Ctx(dims, dev(links), "fp64", antiperiodic_t=antiperiodic) as c:
+def _reference(dims, links, psi, antiperiodic, m_w=1.5):
+    with Ctx(dims, dev(links), "fp64", m_w=m_w, antiperiodic_t=antiperiodic) as c:
         return host(c.wilson(dev(psi)))
 
 
@@ -43,6 +48,41 @@ def test_noalloc_matches_ov_wilson_twice():
         # and against the oracle directly
         oracle_out = np.stack([wilson.wilson(links, p.astype(np.complex128), antiperiodic) for p in psi])
         assert rel(got, oracle_out) < tol
+
+
+def test_noalloc_same_size_twice_allocates_nothing():
+    """Two calls of the same size with different fields and sources: each
+    equals its own ov_wilson result (so nothing of the first call survives in
+    the shared array into the second), and the device's free memory is the
+    same before and after each call (nothing allocated)."""
+    dims = (8, 8, 8, 12)
+    runs = []
+    for seed in (9011, 9013):
+        links = dev(inputs.gauge_links(dims, seed=seed))
+        psi = dev(inputs.gaussian_source(dims, seed=seed + 1))
+        runs.append((links, psi, torch.empty_like(psi), _reference(dims, host(links), host(psi), False)))
+    ov_wilson_noalloc(dims, runs[0][0], runs[0][1], runs[0][2], 1)  # warm-up: address look-up, module load
+    torch.cuda.synchronize()
+    for links, psi, out, want in runs:
+        out.zero_()
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
+        ov_wilson_noalloc(dims, links, psi, out, 1)
+        free_after = torch.cuda.mem_get_info()[0]
+        assert free_after == free_before
+        assert rel(host(out), want) < TOL
+
+
+def test_noalloc_is_independent_of_m_w():
+    """D_W (Eq. 2) has no m_W: ov_wilson on a context made with another m_W
+    gives the same D_W as the entry point, which takes none."""
+    dims = (4, 6, 4, 8)
+    links = inputs.gauge_links(dims, seed=9021)
+    psi = inputs.gaussian_source(dims, seed=9022)
+    out = torch.empty(psi.shape, dtype=torch.complex128, device="cuda")
+    ov_wilson_noalloc(dims, dev(links), dev(psi), out, 1)
+    for m_w in (0.9, 1.5, 1.8):
+        assert rel(host(out), _reference(dims, links, psi, False, m_w=m_w)) < TOL
 
 
 def test_noalloc_rejects_oversize_and_host_memory():
