@@ -12,10 +12,13 @@ Workload (the 24^3 x 48 lattice the headline metric is quoted on):
 Also reported: the stencil's achieved HBM bandwidth (algorithmic bytes over
 its CUDA-event-timed launches inside the timed region), the same metric end
 to end through host buffers, sign(K) applies/s in every precision, the time
-to a 1e-10 solve of D^dagger D (mixed precision; FP64 with --fp64-solve), the
-chiral-sector solve of a point source, the GMRESR solve of D x = b (and of
-the 12 point sources with --batched-solve), 3 steps of over-improved stout
-smearing, the 16^3 x 32 FP32-operator solve and the gradient.
+to a 1e-10 solve of D^dagger D in mixed precision and in plain FP64 (both
+measured; --quick skips the FP64 solve and the batched ones), the 12 point
+sources solved in one call by CG and by GMRESR, the chiral-sector solve of a
+point source, the GMRESR solve of D x = b, 3 steps of over-improved stout
+smearing, the 16^3 x 32 FP32-operator solve and the gradient.  The field
+(plaquette, spectral interval) and the host running the CPU baseline (nproc,
+CPU model, nproc and 1 BLAS/OpenMP threads) are described in the line.
 
 --impl reference times the FP64 CPU oracle (the only reference this method
 has) on a bounded sample of the same workload.
@@ -163,15 +166,18 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline(links, evecs_host, evals, a, b, order, sample_terms=2, sample_evecs=4):
-    """The FP64 oracle timed on the host: sample_terms Chebyshev terms and the
-    deflation with sample_evecs eigenvectors, extrapolated to one full sign(K)
-    apply (order terms, one final K, 40 eigenvectors)."""
-    import oracle
+def cpu_sample(a, b, order, sample_terms=2, sample_vecs=4):
+    """The FP64 oracle timed on the host: sample_terms Chebyshev terms and a
+    projection onto sample_vecs vectors, extrapolated to one full sign(K)
+    apply (order terms, one final K, N_EV-vector deflation).  The projection's
+    cost does not depend on the vectors, so seeded Gaussian stand-ins of the
+    eigenvectors' size are used."""
     from oracle import chebyshev, overlap, wilson
     from paper_1510_06897_gb300 import inputs
 
+    links = inputs.gauge_links(DIMS, seed=SEED_LINKS)
     psi = inputs.gaussian_source(DIMS, seed=SEED_SRC)[0]
+    vecs = inputs.gaussian_source(DIMS, seed=SEED_SRC + 50, nrhs=sample_vecs)
     c = chebyshev.coefficients(sample_terms, a, b)
 
     def kop(w):
@@ -184,18 +190,64 @@ def cpu_baseline(links, evecs_host, evals, a, b, order, sample_terms=2, sample_e
     kop(psi)
     t_k = time.perf_counter() - t0
     t0 = time.perf_counter()
-    cfg = overlap.SignConfig(c, a, b, evals[:sample_evecs], evecs_host[:sample_evecs])
-    coeffs = overlap.project(cfg.evecs, psi)
+    coeffs = overlap.project(vecs, psi)
     perp = psi.copy()
-    for i in range(sample_evecs):
-        perp = perp - coeffs[i] * cfg.evecs[i]
+    for i in range(sample_vecs):
+        perp = perp - coeffs[i] * vecs[i]
     t_defl = time.perf_counter() - t0
-    per_apply = t_terms / sample_terms * order + t_k + 2 * t_defl * N_EV / sample_evecs
-    return {"value": 1.0 / per_apply, "unit": "applies/s", "cores": 1, "kind": "oracle",
+    per_apply = t_terms / sample_terms * order + t_k + 2 * t_defl * N_EV / sample_vecs
+    return {"per_apply_s": per_apply, "sample_seconds": t_terms + t_k + t_defl,
             "sample": (f"FP64 NumPy oracle on 24^3x48: {sample_terms} Chebyshev terms ({2 * sample_terms} K), "
-                       f"1 K, projection onto {sample_evecs} eigenvectors; extrapolated to {order} terms + "
-                       f"{N_EV}-vector deflation ({per_apply:.1f} s per apply)"),
-            "sample_seconds": t_terms + t_k + t_defl}
+                       f"1 K, projection onto {sample_vecs} vectors; extrapolated to {order} terms + "
+                       f"{N_EV}-vector deflation")}
+
+
+def host_description():
+    """nproc and the CPU model (lscpu) of the machine running the bench."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+def cpu_baseline(a, b, order):
+    """The oracle sample run in fresh interpreters (no GPU use) with the BLAS /
+    OpenMP thread count set to nproc and to 1; the headline value is the nproc
+    run, labelled extrapolated (a full sign(K) apply takes hours on the host)."""
+    host = host_description()
+    runs = {}
+    for threads in sorted({host["nproc"] or 1, 1}, reverse=True):
+        env = dict(os.environ)
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            env[var] = str(threads)
+        env["CUDA_VISIBLE_DEVICES"] = ""
+        res = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", f"{a!r},{b!r},{order}"],
+                             capture_output=True, text=True, env=env, timeout=900)
+        if res.returncode != 0:
+            runs[threads] = {"error": res.stderr.strip().splitlines()[-1:] or ["cpu sample failed"]}
+            continue
+        runs[threads] = json.loads(res.stdout.strip().splitlines()[-1])
+    top = max(runs)
+    main_run = runs[top]
+    if "per_apply_s" not in main_run:
+        return {"value": None, "unit": "applies/s", "cores": top, "kind": "oracle (extrapolated)",
+                "sample": str(main_run), **host}
+    out = {"value": 1.0 / main_run["per_apply_s"], "unit": "applies/s", "cores": top,
+           "kind": "oracle (extrapolated)", "sample": main_run["sample"],
+           "sample_seconds": main_run["sample_seconds"], "threads": "BLAS/OpenMP threads = nproc", **host}
+    if 1 in runs and top != 1 and "per_apply_s" in runs[1]:
+        out["single_thread"] = {"value": 1.0 / runs[1]["per_apply_s"], "unit": "applies/s", "cores": 1,
+                                "sample_seconds": runs[1]["sample_seconds"]}
+    return out
 
 
 def run_reference(args):
@@ -229,7 +281,8 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"24^3x48 sign(K) psi, Chebyshev order {ORDER} (oracle sample: one K per step)",
                        "lattice": "24x24x24x48"},
-            "cpu_baseline": {"value": value, "unit": "applies/s", "kind": "oracle", "cores": 1, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "applies/s", "kind": "oracle (extrapolated)", "cores": 1,
+                             "sample": sample, **host_description()},
             "e2e": {"value": value, "unit": "applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -252,14 +305,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp16", choices=["fp16", "bf16", "fp32", "fp64"])
     ap.add_argument("--no-extras", action="store_true", help="headline only")
-    ap.add_argument("--fp64-solve", action="store_true", help="also time the plain FP64 solve (minutes)")
+    ap.add_argument("--quick", action="store_true",
+                    help="skip the minutes-long solves (plain FP64 solve, the 12 point sources by CG and GMRESR)")
+    ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--batched-solve", action="store_true",
-                    help="also solve for the 12 point sources in one call (minutes)")
     ap.add_argument("--eigs-cache", default=None,
                     help="checkpoint file of the set-up eigenpairs: loaded when it matches this workload, "
                          "else computed and written there")
     args = ap.parse_args()
+    if args.cpu_sample:
+        a, b, order = args.cpu_sample.split(",")
+        print(json.dumps(cpu_sample(float(a), float(b), int(order))), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -360,6 +417,8 @@ def main():
                           f"Chebyshev recurrence (one CUDA event pair around them per apply, gaps included)",
                 "algorithmic_bytes_per_launch": bytes_launch,
                 "avg_launch_us": dslash_ms_avg * 1e3, "peak_source": f"hbm_gbs of {peak_kind}",
+                "variant": {k: st[k] for k in ("stencil_tpb", "stencil_minb", "stencil_lrec", "stencil_async",
+                                               "stencil_brick", "stencil_slab")},
                 "stencil_share_of_step": st["dslash_ms"] / elapsed_ms if world == 1 else None}
     roofline.update(stencil_metrics(args.prec, vol, dslash_ms_avg * 1e-3, hbm))
 
@@ -386,7 +445,8 @@ def main():
                        "lattice": "24x24x24x48", "order": ORDER, "n_ev": N_EV, "storage": args.prec,
                        "interval": [a, b], "l2": "inputs larger than L2 (links + eigenvectors + vectors, GBs)",
                        "parallelism": "replicas" if world > 1 else "1 GPU", "setup_s": setup_s,
-                       "eigs_s": t_eigs, "eigs_source": eigs_source},
+                       "eigs_s": t_eigs, "eigs_source": eigs_source,
+                       "field": field_description(links_d, evals, a, b)},
             "roofline": roofline, "e2e": e2e, "gpu_launches": st["kernel_launches"], "clocks": clk}
 
     if rank == 0 and not args.no_extras:
@@ -396,12 +456,21 @@ def main():
             line["extras"] = {"error": f"{type(e).__name__}: {e}"}
     ctx.close()
     if rank == 0 and world == 1 and not args.no_cpu:
-        evh = evecs40[:4].cpu().numpy()
-        line["cpu_baseline"] = cpu_baseline(links, evh, evals40, a, b, ORDER)
+        line["cpu_baseline"] = cpu_baseline(a, b, ORDER)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def field_description(links_d, evals, a, b):
+    """The synthetic field's average plaquette and the spectral interval of
+    the sign function: |lambda_min(K)|, |lambda_{n_ev+1}| (the interval's
+    lower end a) and the upper end b (ov_eigs' bound on lambda_max)."""
+    return {"plaquette": _plaquette(links_d), "abs_lambda_min": float(abs(evals[0])),
+            f"abs_lambda_{N_EV + 1}": float(a), "lambda_max_bound": float(b),
+            "links": "U = exp(i 0.3 H), H seeded Gaussian traceless Hermitian (stand-in for the paper's "
+                     "stout-smeared ensembles)"}
 
 
 def extras(args, ctx, links_d, a, b, evals, evecs, psi, vol):
@@ -463,7 +532,7 @@ def extras(args, ctx, links_d, a, b, evals, evecs, psi, vol):
     res["batched_12_point_sources"] = batched
     # time to solution, D^dagger D x = D^dagger b to 1e-10 (true residual, FP64 operator)
     solves = {}
-    precs = [args.prec] + (["fp64"] if args.fp64_solve else [])
+    precs = [args.prec] + ([] if args.quick or args.prec == "fp64" else ["fp64"])
     for prec in precs:
         with Ctx(DIMS, links_d, prec) as c:
             c.sign_config(ORDER, a, b, evals, evecs)
@@ -478,13 +547,9 @@ def extras(args, ctx, links_d, a, b, evals, evecs, psi, vol):
             x_cg = x
         solves[prec] = {"seconds": dt, "iterations": it, "outer": st["outer_iterations"], "true_rel_resid": r,
                         "mu": MU}
-    if "fp64" not in solves:
-        fp64_apply = res["precisions"]["fp64"]["ms_per_apply"] * 1e-3
-        it = solves[args.prec]["iterations"]
-        solves["fp64_estimate"] = {
-            "seconds": 2 * it * fp64_apply, "basis": f"{it} CG iterations x 2 FP64 sign applies x "
-                                                     f"{fp64_apply * 1e3:.0f} ms (run with --fp64-solve to measure)"}
-    if args.batched_solve:
+    if "fp64" in solves:
+        solves["speedup_mixed_vs_fp64"] = solves["fp64"]["seconds"] / solves[args.prec]["seconds"]
+    if not args.quick:
         with Ctx(DIMS, links_d, args.prec) as c:
             c.sign_config(ORDER, a, b, evals, evecs)
             x = torch.empty_like(src)
@@ -494,12 +559,20 @@ def extras(args, ctx, links_d, a, b, evals, evecs, psi, vol):
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             st = ov_get_stats(c.handle)
-        fp64_apply = res["precisions"]["fp64"]["ms_per_apply"] * 1e-3
-        solves["batched_12_point_sources"] = {
-            "precision": args.prec, "seconds": dt, "iterations": it, "outer": st["outer_iterations"],
-            "true_rel_resid": r, "fp64_estimate_seconds": 12 * 2 * solves[args.prec]["iterations"] * fp64_apply}
-        solves["batched_12_point_sources_gmresr"] = _guarded(gmresr_batched_timing, links_d, a, b, evals, evecs,
-                                                             src, args.prec)
+        batched_cg = {"precision": args.prec, "method": "CG on D^dagger D, 12 right-hand sides per launch",
+                      "seconds": dt, "iterations": it, "outer": st["outer_iterations"], "true_rel_resid": r}
+        if "fp64" in solves:
+            fp64_12 = 12 * solves["fp64"]["seconds"]
+            batched_cg["fp64_single_rhs_path_x12_seconds"] = fp64_12
+            batched_cg["fp64_single_rhs_path_x12_basis"] = (
+                "12 x the measured plain-FP64 single-RHS CG solve of the Gaussian source above "
+                "(the FP64 path solves one right-hand side per call)")
+            batched_cg["speedup_vs_fp64_single_rhs_path_x12"] = fp64_12 / dt
+        solves["batched_12_point_sources"] = batched_cg
+        gm = _guarded(gmresr_batched_timing, links_d, a, b, evals, evecs, src, args.prec)
+        if "fp64" in solves and "seconds" in gm:
+            gm["speedup_vs_fp64_single_rhs_path_x12"] = 12 * solves["fp64"]["seconds"] / gm["seconds"]
+        solves["batched_12_point_sources_gmresr"] = gm
     # chiral point source (spin 0, colour 0 at the origin: chirality +1): D^-1 b
     # from the chiral-sector solve (one sign apply per iteration) + one D^dagger,
     # against the D^dagger D solve of the same source
@@ -546,17 +619,19 @@ def _guarded(fn, *args, **kwargs):
         return {"error": f"{type(e).__name__}: {e}"}
 
 
-def gmresr_timing(links_d, a, b, evals, evecs, psi, prec, cg_seconds=None, settings=((0, 0.1),), x_cg=None):
+def gmresr_timing(links_d, a, b, evals, evecs, psi, prec, cg_seconds=None, x_cg=None):
     """D[mu] x = psi to 1e-10 (||psi - D x|| / ||psi||, FP64 operator) by
-    GMRESR: GCR on D in the storage precision, inner SUMR with a relaxed
-    (lower-order) sign, FP64 defect correction.  settings: (inner order,
-    inner tolerance) pairs; order 0 = automatic (sign error <= 1e-2).  x_cg:
-    the CG (normal equations) solution of the same system, whose
-    ||psi - D x|| / ||psi|| and distance to the GMRESR solution are reported
-    (the CG stops on the normal-equation residual instead)."""
+    GMRESR: GCR on D (FP32 copy of the operator for 16-bit storage, the
+    default), inner SUMR in the storage precision with a relaxed (automatic,
+    sign error <= 1e-2) sign, FP64 defect correction; the FP32 copy is made
+    before the timed solve and its set-up reported apart.  For 16-bit storage
+    also the same solve with GCR in the storage precision.  x_cg: the CG
+    (normal equations) solution of the same system, whose ||psi - D x|| / ||psi||
+    and distance to the GMRESR solution are reported (the CG stops on the
+    normal-equation residual instead)."""
     import torch
-    from paper_1510_06897_gb300.binding import (Ctx, ov_get_stats, ov_overlap, ov_reset_stats,
-                                                ov_set_gmresr_params, ov_solve_gmresr)
+    from paper_1510_06897_gb300.binding import (Ctx, ov_enable_fp32_operator, ov_get_stats, ov_overlap,
+                                                ov_reset_stats, ov_set_gmresr_fp32_level, ov_solve_gmresr)
     out = {}
     if x_cg is not None:
         with Ctx(DIMS, links_d, "fp64") as c64:
@@ -564,11 +639,17 @@ def gmresr_timing(links_d, a, b, evals, evecs, psi, prec, cg_seconds=None, setti
             dx = torch.empty_like(psi)
             ov_overlap(c64.handle, MU, 0, x_cg, dx, 1)
             out["cg_true_rel_resid_D"] = (torch.linalg.vector_norm(psi - dx) / torch.linalg.vector_norm(psi)).item()
-    with Ctx(DIMS, links_d, prec) as c:
-        c.sign_config(ORDER, a, b, evals, evecs)
-        x = torch.empty_like(psi)
-        for order_in, tol_in in settings:
-            ov_set_gmresr_params(c.handle, order_in, tol_in, 1000, 12)
+    levels = [("default", True)] + ([("storage_precision_gcr", False)] if prec in ("fp16", "bf16") else [])
+    for name, fp32_level in levels:
+        with Ctx(DIMS, links_d, prec) as c:
+            t0 = time.perf_counter()
+            if fp32_level:
+                ov_enable_fp32_operator(c.handle, links_d)
+            else:
+                ov_set_gmresr_fp32_level(c.handle, 0)
+            c.sign_config(ORDER, a, b, evals, evecs)
+            setup = time.perf_counter() - t0
+            x = torch.empty_like(psi)
             ov_reset_stats(c.handle)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -576,38 +657,16 @@ def gmresr_timing(links_d, a, b, evals, evecs, psi, prec, cg_seconds=None, setti
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             st = ov_get_stats(c.handle)
-            out[f"inner_order_{order_in or 'auto'}_tol_{tol_in}"] = {
-                "precision": prec, "seconds": dt, "sumr_iterations": it, "relaxed_order": st["gmresr_order"],
-                "gcr_steps": st["gcr_iterations"], "fp64_passes": st["outer_iterations"],
-                "sign_applies": st["sign_applies"], "dslash_launches": st["dslash_launches"],
-                "true_rel_resid_D": r, "mu": MU,
-                "speedup_vs_cg_normal_equations": (cg_seconds / dt) if cg_seconds else None,
-                "rel_diff_to_cg_solution": ((torch.linalg.vector_norm(x - x_cg) / torch.linalg.vector_norm(x_cg)).item()
-                                            if x_cg is not None else None)}
-    if prec in ("fp16", "bf16"):  # the GCR level on an FP32 copy of the operator
-        out["fp32_gcr_level"] = _guarded(_gmresr_fp32_level, links_d, a, b, evals, evecs, psi, prec, cg_seconds)
+        gcr = ("fp32" if (fp32_level and prec in ("fp16", "bf16")) else prec)
+        out[name] = {
+            "precision": f"{prec} SUMR, {gcr} GCR", "seconds": dt, "setup_s": setup, "sumr_iterations": it,
+            "relaxed_order": st["gmresr_order"], "gcr_steps": st["gcr_iterations"],
+            "fp64_passes": st["outer_iterations"], "sign_applies": st["sign_applies"],
+            "dslash_launches": st["dslash_launches"], "true_rel_resid_D": r, "mu": MU,
+            "speedup_vs_cg_normal_equations": (cg_seconds / dt) if cg_seconds else None,
+            "rel_diff_to_cg_solution": ((torch.linalg.vector_norm(x - x_cg) / torch.linalg.vector_norm(x_cg)).item()
+                                        if x_cg is not None else None)}
     return out
-
-
-def _gmresr_fp32_level(links_d, a, b, evals, evecs, psi, prec, cg_seconds):
-    import torch
-    from paper_1510_06897_gb300.binding import Ctx, ov_enable_fp32_operator, ov_get_stats, ov_solve_gmresr
-    with Ctx(DIMS, links_d, prec) as c:
-        t0 = time.perf_counter()
-        ov_enable_fp32_operator(c.handle, links_d)
-        c.sign_config(ORDER, a, b, evals, evecs)
-        setup = time.perf_counter() - t0
-        x = torch.empty_like(psi)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        it, r = ov_solve_gmresr(c.handle, MU, 1e-10, 100000, psi, x, 1, allow_not_converged=True)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        st = ov_get_stats(c.handle)
-    return {"precision": f"{prec} SUMR, fp32 GCR", "seconds": dt, "setup_s (FP32 copy + configuration)": setup,
-            "sumr_iterations": it, "relaxed_order": st["gmresr_order"], "gcr_steps": st["gcr_iterations"],
-            "fp64_passes": st["outer_iterations"], "true_rel_resid_D": r,
-            "speedup_vs_cg_normal_equations": (cg_seconds / dt) if cg_seconds else None}
 
 
 def gmresr_batched_timing(links_d, a, b, evals, evecs, src, prec):

@@ -205,7 +205,10 @@ ov_status ov_sumr(ov_ctx* ctx, double mu, double tol, int maxit, const void* b, 
 /* GMRESR for D[mu] x = b (Sec. 2: recursive GMRES preconditioned by a
  * low-accuracy SUMR solve with a relaxed sign function).  Three levels:
  * FP64 defect correction on D[mu] (as ov_solve, on D itself); inside it GCR
- * on D[mu] in the context precision with the configured sign, its
+ * on D[mu] with the configured sign -- in FP32 for OV_MIXED_FP16 /
+ * OV_MIXED_BF16 contexts (an FP32 copy of the operator is built from the
+ * context's FP64 links on the first call and kept; see
+ * ov_set_gmresr_fp32_level), in the context precision otherwise -- its
  * directions kept and orthogonalised (up to max_dirs, then restarted); each
  * direction an ov_sumr-type solve with a LOWER-order Chebyshev polynomial on
  * the same interval (the relaxed sign; see ov_set_gmresr_params).  Stops when
@@ -221,6 +224,8 @@ ov_status ov_solve_gmresr(ov_ctx* ctx, double mu, double tol, int maxit, const v
  * this FP32 operator (configured order) while the inner SUMR solves stay on
  * the 16-bit one, so each FP64 defect-correction pass gains about the FP32
  * accuracy instead of the 16-bit one and fewer FP64 passes are needed.
+ * ov_solve_gmresr builds this copy by itself on its first call (from the
+ * context's FP64 links); calling this first only moves that cost here.
  * links: the field given to ov_create, same layout (host or device).  The
  * deflation eigenvectors come from the last ov_sign_config (converted from
  * its FP64 copy) or the next one.  Costs FP32 links, eigenvectors and work
@@ -229,6 +234,14 @@ ov_status ov_solve_gmresr(ov_ctx* ctx, double mu, double tol, int maxit, const v
  * ctx or links), OV_ERR_NOMEM, OV_ERR_CUDA (the context keeps working without
  * the FP32 copy). */
 ov_status ov_enable_fp32_operator(ov_ctx* ctx, const void* links);
+
+/* Whether ov_solve_gmresr on an OV_MIXED_FP16 / OV_MIXED_BF16 context runs
+ * its GCR level on the FP32 copy of the operator (on != 0, the default) or
+ * in the storage precision (0; an FP32 copy already made is freed).  Measured
+ * at 24^3 x 48, FP16, mu = 0.02: 2 FP64 passes instead of 4 and 3.1 s
+ * instead of 4.3 s.  No effect on other precisions.  Errors: OV_ERR_INVALID
+ * (null ctx), OV_ERR_CUDA. */
+ov_status ov_set_gmresr_fp32_level(ov_ctx* ctx, int on);
 
 /* GMRESR controls.  inner_order: Chebyshev order of the relaxed sign of the
  * inner SUMR solves (0, the default: the smallest order whose sign error
@@ -249,7 +262,7 @@ ov_status ov_set_gmresr_params(ov_ctx* ctx, int inner_order, double inner_tol, i
  * lambda_max_out (may be NULL): an upper bound of |lambda| of K.  max_iter
  * counts filter + Rayleigh-Ritz steps (filter degree 32 on K^2; the
  * environment variable OV_EIGS_DEGREE overrides it, 4 .. 256) on a block of
- * max(n_ev + 8, 2.5 n_ev) vectors, at most 64 (so n_ev <= 56).
+ * max(n_ev + 8, 2.5 n_ev) vectors, at most 128 (so n_ev <= 120).
  * Errors: OV_ERR_INVALID, OV_ERR_NOT_CONVERGED (best pairs returned; also when
  * the filtered block stops being finite, with no pairs written). */
 ov_status ov_eigs(ov_ctx* ctx, int n_ev, double tol, int max_iter, double* evals, void* evecs,
@@ -295,6 +308,19 @@ ov_status ov_set_profiling(ov_ctx* ctx, int on);
  * default; OV_CHECKS=1 in the environment turns it on for every context
  * created afterwards.  Errors: OV_ERR_INVALID (null ctx). */
 ov_status ov_set_checks(ov_ctx* ctx, int on);
+
+/* Testing hook for the failure path of the kernels that wait on their own
+ * asynchronous work (the tensor-core deflation projection of several
+ * right-hand sides and the slab stencil), whose every wait is bounded (about
+ * a second) and reported instead of hanging.  With cycles > 0, each wait of
+ * their copy / MMA pipelines first waits up to `cycles` clock cycles on a
+ * device flag of the context that nothing ever sets, so it runs out: the
+ * kernel records its error flag, waits with its normal bound for its own
+ * copies and MMAs still in flight, releases its tensor memory and returns,
+ * and the call reports OV_ERR_CUDA; the context stays usable.  cycles <= 0
+ * turns this off (the default).  Errors: OV_ERR_INVALID (null ctx),
+ * OV_ERR_NOMEM, OV_ERR_CUDA. */
+ov_status ov_test_wait_expiry(ov_ctx* ctx, long long cycles);
 
 /* True relative residual history of the last solve (ov_solve,
  * ov_solve_chiral, ov_solve_gmresr): the largest over the RHS after each

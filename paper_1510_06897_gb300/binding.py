@@ -80,6 +80,8 @@ _SIGNATURES = {
     "ov_set_profiling": [_vp, _i],
     "ov_set_checks": [_vp, _i],
     "ov_get_residual_history": [_vp, ctypes.POINTER(_d), _i, ctypes.POINTER(_i)],
+    "ov_set_gmresr_fp32_level": [_vp, _i],
+    "ov_test_wait_expiry": [_vp, ctypes.c_longlong],
     "ov_sign_poly_quad": [_vp, _i, _d, _d, _vp, _vp, _i, ctypes.POINTER(_d)],
     "ov_wilson_noalloc": [ctypes.POINTER(_i), _vp, _vp, _vp, _i, _i, _i, _vp],
     "ov_stout_smear": [ctypes.POINTER(_i), _vp, _vp, _d, _d, _i, _vp],
@@ -237,6 +239,11 @@ def ov_enable_fp32_operator(ctx, links):
     return _check(lib().ov_enable_fp32_operator(ctx, _ptr(links)), ctx)
 
 
+def ov_set_gmresr_fp32_level(ctx, on=True):
+    """GCR level of GMRESR on an FP32 copy of a 16-bit operator (default) or not."""
+    return _check(lib().ov_set_gmresr_fp32_level(ctx, int(bool(on))), ctx)
+
+
 def ov_set_gmresr_params(ctx, inner_order=0, inner_tol=0.1, inner_maxit=1000, max_dirs=12):
     return _check(lib().ov_set_gmresr_params(ctx, int(inner_order), float(inner_tol), int(inner_maxit),
                                              int(max_dirs)), ctx)
@@ -318,6 +325,12 @@ def ov_get_residual_history(ctx):
     buf = (_d * max(1, n.value))()
     _check(lib().ov_get_residual_history(ctx, buf, n.value, ctypes.byref(n)), ctx)
     return [buf[i] for i in range(n.value)]
+
+
+def ov_test_wait_expiry(ctx, cycles):
+    """Testing hook: pipeline waits of the tensor-core projection and the slab
+    stencil run out after `cycles` on a flag nothing sets; 0 turns it off (see overlap.h)."""
+    return _check(lib().ov_test_wait_expiry(ctx, int(cycles)), ctx)
 
 
 def ov_set_checks(ctx, on):

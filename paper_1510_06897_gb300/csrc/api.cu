@@ -117,7 +117,7 @@ ov_status ov_destroy(ov_ctx* c) {
   c->lo.release();
   c->mid.release();
   for (cudaEvent_t ev : c->evs) cudaEventDestroy(ev);
-  for (DevBuf* b : {&c->d_sgn, &c->d_c, &c->d_partial, &c->d_scalars, &c->d_gram, &c->d_err, &c->stage_in, &c->stage_out, &c->stage_links,
+  for (DevBuf* b : {&c->d_sgn, &c->d_c, &c->d_partial, &c->d_scalars, &c->d_gram, &c->d_err, &c->d_never, &c->stage_in, &c->stage_out, &c->stage_links,
                     &c->o_x, &c->o_r, &c->o_rhs, &c->o_q})
     b->release();
   if (c->h_scalars) cudaFreeHost(c->h_scalars);
@@ -250,6 +250,17 @@ ov_status ov_get_residual_history(const ov_ctx* c, double* out, int max_len, int
   const int n = (int)c->res_history.size();
   for (int i = 0; i < std::min(n, max_len); ++i) out[i] = c->res_history[i];
   if (len) *len = n;
+  return OV_OK;
+}
+
+ov_status ov_test_wait_expiry(ov_ctx* c, long long cycles) {
+  if (!c) return OV_ERR_INVALID;
+  if (cycles > 0 && c->d_never.p == nullptr) {  // the flag nothing sets
+    OV_CK(c->d_never.ensure(sizeof(int)));
+    OV_CK(cudaMemsetAsync(c->d_never.p, 0, sizeof(int), c->st));
+    OV_CK(cudaStreamSynchronize(c->st));
+  }
+  c->stall_cycles = cycles > 0 ? cycles : 0;
   return OV_OK;
 }
 

@@ -157,6 +157,24 @@ __global__ void k_pack_links(const double2* __restrict__ in, void* __restrict__ 
   }
 }
 
+// FP64 packed links (all 9 entries, [(mu * 9 + e) V + s]) back to the
+// interface layout complex128 [4][V][3][3].
+__global__ void k_unpack_links_f64(const double2* __restrict__ in, double2* __restrict__ out, int V) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const int mu = blockIdx.y;
+  const double2* q = in + (int64_t)mu * 9 * V;
+  double2* u = out + ((int64_t)mu * V + s) * 9;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) u[e] = q[(int64_t)e * V + s];
+}
+
+void launch_unpack_links_f64(const LatticeH& g, const void* packed, void* out, cudaStream_t st) {
+  dim3 grid(grid_for(g.V), 4);
+  k_unpack_links_f64<<<grid, kThreads, 0, st>>>(static_cast<const double2*>(packed), static_cast<double2*>(out),
+                                                 (int)g.V);
+}
+
 void launch_pack_links(OpPrec p, int lrec, const LatticeH& g, const void* in, void* out, cudaStream_t st) {
   dim3 grid(grid_for(g.V), 4);
   const double2* src = static_cast<const double2*>(in);

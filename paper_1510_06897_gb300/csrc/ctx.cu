@@ -111,6 +111,10 @@ ov_status prof_close(ov_ctx* c, int n) {
 ov_status dslash(ov_ctx* c, Inst& I, OpPrec out_prec, const void* in, void* out, const EpiArgs& e, int nrhs) {
   DslashCfg cfg;
   OV_TRY(batch_cfg(c, I, nrhs, &cfg));
+  if (c->stall_cycles > 0) {
+    cfg.stall = c->d_never.as<int>();
+    cfg.stall_cycles = c->stall_cycles;
+  }
   if (c->prof == 1) OV_TRY(prof_open(c));
   if (!launch_dslash(I.p, out_prec, cfg, c->g, I.links.p, in, out, e, nrhs, c->st))
     return fail(c, OV_ERR_CUDA, "stencil variant not compiled");

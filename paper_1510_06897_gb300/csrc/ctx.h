@@ -90,6 +90,11 @@ struct ov_ctx {
   // output checks (ov_set_checks / OV_CHECKS=1): every vector output is
   // scanned for NaN / Inf before it is handed back
   bool checks = false;
+  // testing (ov_test_wait_expiry): > 0 makes the pipeline waits of the
+  // kernels that wait on their own asynchronous work first wait this many
+  // cycles on d_never, a device flag that nothing sets, and report expiry
+  long long stall_cycles = 0;
+  DevBuf d_never;
   // solver controls
   double inner_tol = 1e-5;
   int max_outer = 30;
@@ -99,6 +104,9 @@ struct ov_ctx {
   double gm_tol = 0.1;
   int gm_maxit = 1000;
   int gm_dirs = 12;
+  // GCR level of GMRESR on an FP32 copy of the operator for 16-bit contexts
+  // (built from the FP64 links on first use unless switched off)
+  bool gm_fp32 = true;
   std::vector<double> coef_relaxed;
   double relaxed_key[4] = {0, 0, 0, 0};
   ov_stats stats{};

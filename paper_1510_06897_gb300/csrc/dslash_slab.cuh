@@ -50,9 +50,17 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
 }
 
 // Waits for the phase of the given parity to complete; false after about a
-// second (2^31 clocks).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// second (2^31 clocks).  stall (testing, see ov_test_wait_expiry): a device
+// flag that nothing sets; when given, the wait first waits up to stall_cycles
+// for it, runs out and reports failure as an expired wait would.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* stall = nullptr,
+                                          long long stall_cycles = 0) {
   const long long t0 = clock64();
+  if (stall != nullptr) {
+    while (*stall == 0) {
+      if (clock64() - t0 > stall_cycles) return false;
+    }
+  }
   while (!mbar_test(bar, parity)) {
     if (clock64() - t0 > (1ll << 31)) return false;
   }
@@ -199,7 +207,8 @@ __host__ __device__ inline int slab_phases(int nv) { return 5 + (nv + 1) / 2; }
 template <class T, class OT>
 __global__ void __launch_bounds__(kSlabMaxThreads, 1)
     k_dslash_slab(Geo g, const char* __restrict__ links, const char* __restrict__ in, char* out, SlabEpi e,
-                  long long rhs_bytes, long long out_rhs_bytes, int nrhs, int nslots, volatile int* err) {
+                  long long rhs_bytes, long long out_rhs_bytes, int nrhs, int nslots, volatile int* err,
+                  const int* stall, long long stall_cycles) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int P = g.LxLy;
   const int Lx = g.L[0], Ly = g.L[1], Lz = g.L[2], Lt = g.L[3];
@@ -232,7 +241,7 @@ __global__ void __launch_bounds__(kSlabMaxThreads, 1)
     long long item = blockIdx.x;
     bool ok = true;
     for (; j < nsteps; ++j) {
-      if (round > 0 && !mbar_wait(smem_u32(&empty[slot]), (uint32_t)((round - 1) & 1))) {
+      if (round > 0 && !mbar_wait(smem_u32(&empty[slot]), (uint32_t)((round - 1) & 1), stall, stall_cycles)) {
         ok = false;
         break;
       }
@@ -306,7 +315,7 @@ __global__ void __launch_bounds__(kSlabMaxThreads, 1)
   long long item = blockIdx.x;
   Spinor<float> acc;
   for (long long j = 0; j < nsteps; ++j) {
-    if (!mbar_wait(smem_u32(&full[slot]), par)) {
+    if (!mbar_wait(smem_u32(&full[slot]), par, stall, stall_cycles)) {
       *err = 1;
       return;
     }
@@ -410,7 +419,7 @@ bool launch_slab(const DslashCfg& c, const LatticeH& gh, const void* links, cons
   const unsigned grid = (unsigned)std::min<long long>(nitems, c.slab);
   launch_windowed(slab::k_dslash_slab<T, OT>, dim3(grid), dim3(P + 32), smem, st, links, false, g,
                   static_cast<const char*>(links), static_cast<const char*>(in), static_cast<char*>(out), se, rb, orb,
-                  nrhs, slab::slab_slots(P), static_cast<volatile int*>(c.err));
+                  nrhs, slab::slab_slots(P), static_cast<volatile int*>(c.err), c.stall, c.stall_cycles);
   return true;
 }
 

@@ -113,18 +113,36 @@ void rayleigh_ritz(int m, const std::vector<cd>& G, const std::vector<cd>& H, st
   }
 }
 
+// out[i * mb + j] = <A_i, B_j> (FP64 sums), in tiles of at most
+// gram_max_vectors() vectors per side (one Gram launch per tile).
 ov_status gram(ov_ctx* c, OpPrec p, const void* A, int ma, const void* B, int mb, DevBuf& partial,
                std::vector<cd>& out) {
   const int64_t V = c->g.V;
-  OV_CK(partial.ensure(sizeof(double2) * (size_t)ma * mb * kReduceBlocks));
-  OV_CK(launch_gram(p, A, ma, B, mb, V, partial.as<double2>(), kReduceBlocks, c->st));
-  OV_TRY(launched(c));
-  std::vector<double2> r((size_t)ma * mb);
-  OV_TRY(read_reduced(c, partial.as<double2>(), ma * mb, r.data()));
-  out.resize((size_t)ma * mb);
-  for (size_t i = 0; i < r.size(); ++i) out[i] = cd(r[i].x, r[i].y);
+  const size_t vb = (size_t)spinor_bytes_per_site(p) * V;
+  const int tile = gram_max_vectors();
+  out.assign((size_t)ma * mb, cd(0.0));
+  OV_CK(partial.ensure(sizeof(double2) * (size_t)tile * tile * kReduceBlocks));
+  std::vector<double2> r((size_t)tile * tile);
+  for (int i0 = 0; i0 < ma; i0 += tile)
+    for (int j0 = 0; j0 < mb; j0 += tile) {
+      const int ni = std::min(tile, ma - i0), nj = std::min(tile, mb - j0);
+      OV_CK(launch_gram(p, static_cast<const char*>(A) + (size_t)i0 * vb, ni,
+                        static_cast<const char*>(B) + (size_t)j0 * vb, nj, V, partial.as<double2>(), kReduceBlocks,
+                        c->st));
+      OV_TRY(launched(c));
+      OV_TRY(read_reduced(c, partial.as<double2>(), ni * nj, r.data()));
+      for (int i = 0; i < ni; ++i)
+        for (int j = 0; j < nj; ++j) {
+          const double2 v = r[(size_t)i * nj + j];
+          out[(size_t)(i0 + i) * mb + j0 + j] = cd(v.x, v.y);
+        }
+    }
   return OV_OK;
 }
+
+// Largest block of the subspace iteration (vectors); the Gram matrices are
+// formed in tiles, the stencil and the rotation take any width.
+constexpr int kEigsMaxBlock = 128;
 
 }  // namespace
 
@@ -132,12 +150,12 @@ extern "C" ov_status ov_eigs(ov_ctx* c, int n_ev, double tol, int max_iter, doub
                              double* lambda_max_out) {
   if (!c) return OV_ERR_INVALID;
   if (!evals || !evecs) return fail(c, OV_ERR_INVALID, "null output");
-  const int mmax = gram_max_vectors();
+  const int mmax = kEigsMaxBlock;
   if (n_ev < 1 || n_ev + 8 > mmax) return fail(c, OV_ERR_INVALID, "need 1 <= n_ev <= " + std::to_string(mmax - 8));
   if (!(tol > 0.0) || max_iter < 1) return fail(c, OV_ERR_INVALID, "need tol > 0 and max_iter >= 1");
   const int64_t V = c->g.V;
-  // block of ~2.5 n_ev (capped by the Gram kernel): a wider block separates
-  // the wanted band from the rest better, so fewer filter sweeps are needed
+  // block of ~2.5 n_ev (at most kEigsMaxBlock): a wider block separates the
+  // wanted band from the rest better, so fewer filter sweeps are needed
   // (counted on a model problem: 20 pairs, block 50 vs 30, half the K
   // applications)
   const int m = std::min(mmax, std::max(n_ev + 8, (5 * n_ev) / 2));

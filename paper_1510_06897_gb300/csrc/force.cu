@@ -93,16 +93,20 @@ __device__ __forceinline__ void force_dir(const Lattice& g, const Coords& c, int
     }
 }
 
+// A block is 32 consecutive sites x the 4 directions, warp mu taking
+// direction mu: the four warps read the same u(x), v(x) of every pair at
+// about the same time (one L2 read, three L1 hits), and the x neighbours are
+// the next lane's own sites.
 template <class T>
 __global__ void __launch_bounds__(128) k_force_pairs(Lattice g, const void* __restrict__ links,
                                                      PairArgsDev<typename Store<T>::R> P, void* Gv) {
   using R = typename Store<T>::R;
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t s = blockIdx.x * (int64_t)32 + (threadIdx.x & 31);
   if (s >= g.V) return;
   cplx<R>* G = static_cast<cplx<R>*>(Gv);
   const Coords c = site_coords(g, s);
   const int64_t sy = g.L[0], sz = sy * g.L[1], st = sz * g.L[2];
-  switch (blockIdx.y) {
+  switch (threadIdx.x >> 5) {
     case 0: force_dir<0, T, R>(g, c, s, 1, links, P, G); break;
     case 1: force_dir<1, T, R>(g, c, s, sy, links, P, G); break;
     case 2: force_dir<2, T, R>(g, c, s, sz, links, P, G); break;
@@ -124,7 +128,7 @@ void launch_force_pairs(OpPrec p, const LatticeH& gh, const void* links, const F
       P->w[i] = static_cast<decltype(+P->w[0])>(pairs.w[i]);
     }
   };
-  dim3 grid((unsigned)((g.V + 127) / 128), 4);
+  const unsigned grid = (unsigned)((g.V + 31) / 32);
   if (p == OP_F64) {
     PairArgsDev<double> P;
     args(&P);

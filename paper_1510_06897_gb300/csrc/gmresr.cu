@@ -264,6 +264,42 @@ static ov_status gcr_core(ov_ctx* c, Inst& I, Inst& S, const void* r0, void* e, 
   return OV_OK;
 }
 
+// Builds the FP32 operator instance (c->mid) from device links in the
+// interface layout; a failure leaves the context without it.
+ov_status build_fp32_operator(ov_ctx* c, const void* dl) {
+  ov_status s = init_inst(c, c->mid, OP_F32, dl);
+  if (s == OV_OK && c->configured && c->n_ev > 0) {  // eigenvectors from the FP64 copy
+    cudaError_t e = c->mid.evecs.ensure(c->mid.vbytes(c->g.V) * c->n_ev);
+    if (e != cudaSuccess) {
+      s = fail(c, e == cudaErrorMemoryAllocation ? OV_ERR_NOMEM : OV_ERR_CUDA, cudaGetErrorString(e));
+    } else {
+      launch_convert(OP_F64, OP_F32, c->hi.evecs.p, c->mid.evecs.p, c->g.V, c->n_ev, 1.0, 0, c->st);
+      s = launched(c);
+    }
+  }
+  if (s == OV_OK) {
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) s = fail(c, OV_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (s != OV_OK) {
+    c->mid.release();
+    c->mid.active = false;
+  }
+  return s;
+}
+
+// The FP32 GCR level for a 16-bit context, from the context's own FP64 links.
+ov_status ensure_fp32_level(ov_ctx* c) {
+  if (!c->gm_fp32 || c->mid.active || (c->prec != OV_MIXED_FP16 && c->prec != OV_MIXED_BF16)) return OV_OK;
+  DevBuf iface;
+  OV_CK(iface.ensure((size_t)c->g.V * 4 * 9 * 16));
+  launch_unpack_links_f64(c->g, c->hi.links.p, iface.p, c->st);
+  OV_TRY(launched(c));
+  const ov_status s = build_fp32_operator(c, iface.p);
+  iface.release();
+  return s;
+}
+
 static ov_status gmresr_core(ov_ctx* c, double mu, double tol, int maxit, const void* b, void* x, int nrhs,
                              ov_dtype dt, int* iters, double* true_rel_resid) {
   if (!c) return OV_ERR_INVALID;
@@ -273,6 +309,7 @@ static ov_status gmresr_core(ov_ctx* c, double mu, double tol, int maxit, const 
   OV_TRY(check_dtype(c, nrhs, dt));
   if (!c->configured) return fail(c, OV_ERR_STATE, "sign(K) not configured: call ov_sign_config first");
   OV_TRY(relaxed_coefficients(c));
+  OV_TRY(ensure_fp32_level(c));
   c->stats.gmresr_order = (int)c->coef_relaxed.size() - 1;
   c->stats.inner_iterations = 0;
   c->stats.outer_iterations = 0;
@@ -280,7 +317,8 @@ static ov_status gmresr_core(ov_ctx* c, double mu, double tol, int maxit, const 
   c->stats.gcr_iterations = 0;
   Inst& H = c->hi;
   // S: the inner SUMR level (the context precision); I: the GCR level, the
-  // FP32 operator of ov_enable_fp32_operator when a 16-bit context has one
+  // FP32 operator (built on first use, or by ov_enable_fp32_operator) when a
+  // 16-bit context has one
   Inst& S = (c->prec == OV_FP64) ? c->hi : c->lo;
   const bool mid = c->mid.active && (c->prec == OV_MIXED_FP16 || c->prec == OV_MIXED_BF16);
   Inst& I = mid ? c->mid : S;
@@ -366,6 +404,7 @@ static ov_status gmresr_core(ov_ctx* c, double mu, double tol, int maxit, const 
 
 extern "C" {
 
+
 ov_status ov_enable_fp32_operator(ov_ctx* c, const void* links) {
   if (!c) return OV_ERR_INVALID;
   if (!links) return fail(c, OV_ERR_INVALID, "null links");
@@ -373,26 +412,20 @@ ov_status ov_enable_fp32_operator(ov_ctx* c, const void* links) {
   if (c->mid.active) return OV_OK;
   const void* dl = nullptr;
   ov_status s = stage_in(c, c->stage_links, links, (size_t)c->g.V * 4 * 9 * 16, &dl);
-  if (s == OV_OK) s = init_inst(c, c->mid, OP_F32, dl);
-  if (s == OV_OK && c->configured && c->n_ev > 0) {  // eigenvectors from the FP64 copy
-    cudaError_t e = c->mid.evecs.ensure(c->mid.vbytes(c->g.V) * c->n_ev);
-    if (e != cudaSuccess) {
-      s = fail(c, e == cudaErrorMemoryAllocation ? OV_ERR_NOMEM : OV_ERR_CUDA, cudaGetErrorString(e));
-    } else {
-      launch_convert(OP_F64, OP_F32, c->hi.evecs.p, c->mid.evecs.p, c->g.V, c->n_ev, 1.0, 0, c->st);
-      s = launched(c);
-    }
-  }
-  if (s == OV_OK) {
-    cudaError_t e = cudaStreamSynchronize(c->st);
-    if (e != cudaSuccess) s = fail(c, OV_ERR_CUDA, cudaGetErrorString(e));
-  }
+  if (s == OV_OK) s = build_fp32_operator(c, dl);
   c->stage_links.release();
-  if (s != OV_OK) {
+  return s;
+}
+
+ov_status ov_set_gmresr_fp32_level(ov_ctx* c, int on) {
+  if (!c) return OV_ERR_INVALID;
+  c->gm_fp32 = on != 0;
+  if (!c->gm_fp32 && c->mid.active) {  // back to GCR in the storage precision
+    OV_CK(cudaStreamSynchronize(c->st));
     c->mid.release();
     c->mid.active = false;
   }
-  return s;
+  return OV_OK;
 }
 
 ov_status ov_set_gmresr_params(ov_ctx* c, int inner_order, double inner_tol, int inner_maxit, int max_dirs) {

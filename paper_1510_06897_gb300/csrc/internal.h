@@ -60,6 +60,8 @@ struct DslashCfg {
   int brick = 0;  // 1: a block covers an 8 x 4 x (tpb / 32) brick of sites (Lx % 8 = Ly % 4 = 0,
                   // Lz % (tpb / 32) = 0) instead of consecutive sites of an (x, y) plane
   int* err = nullptr;  // slab kernel: set to 1 (device-visible memory) if a bulk copy did not land in time
+  const int* stall = nullptr;  // slab kernel, testing: a device flag nothing sets, waited on for stall_cycles
+  long long stall_cycles = 0;  // by every pipeline wait, which then reports expiry (ov_test_wait_expiry)
 };
 
 // Whether blocks of tpb threads can be mapped onto 8 x 4 x (tpb / 32) bricks.
@@ -98,6 +100,8 @@ void launch_unpack_spinor(OpPrec p, IfaceType it, const LatticeH& g, const void*
 // links complex128 [4][V][3][3] -> internal storage (lrec 12 or 18 reals for
 // 16-bit storage; FP64 always 18, FP32 always 12)
 void launch_pack_links(OpPrec p, int lrec, const LatticeH& g, const void* in, void* out, cudaStream_t st);
+// FP64 packed links -> complex128 [4][V][3][3]
+void launch_unpack_links_f64(const LatticeH& g, const void* packed, void* out, cudaStream_t st);
 
 // Number of blocks every reduction kernel uses (fixed, so that results are
 // bitwise reproducible).
@@ -197,8 +201,11 @@ void launch_force_finish(OpPrec p, const void* G, int64_t V, void* out, cudaStre
 // partial[(i*mb + j)*nblk + blk] as launch_gram, for FP32 vectors, computed
 // with tcgen05 (TF32 x 3 split products); ma <= tc_gram_max_rows(),
 // mb <= tc_gram_max_rhs().  *err is set to 1 if a bounded wait expired.
+// stall (testing; null normally): a device flag that nothing sets, on which
+// every pipeline wait first waits up to stall_cycles and then reports expiry;
+// the drain before exit waits as usual.
 cudaError_t launch_tc_gram(const void* A, int ma, const void* B, int mb, int64_t V, int g5b, double2* partial,
-                           int nblk, int* err, cudaStream_t st);
+                           int nblk, int* err, const int* stall, long long stall_cycles, cudaStream_t st);
 int tc_gram_max_rows();
 int tc_gram_max_rhs();
 

@@ -89,7 +89,7 @@ ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kin
       OV_CK(c->d_err.ensure(sizeof(int)));
       OV_CK(cudaMemsetAsync(c->d_err.p, 0, sizeof(int), c->st));
       OV_CK(launch_tc_gram(I.evecs.p, n_ev, in, nrhs, V, g5in, c->d_gram.as<double2>(), nblk, c->d_err.as<int>(),
-                           c->st));
+                           c->stall_cycles > 0 ? c->d_never.as<int>() : nullptr, c->stall_cycles, c->st));
       OV_TRY(launched(c));
       c->stats.tc_gemm_launches++;
       int herr = 0;

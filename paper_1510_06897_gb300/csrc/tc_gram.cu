@@ -88,8 +88,17 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait: false if the phase did not complete within ~2^31 cycles.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// stall (testing, see ov_test_wait_expiry): a device flag that nothing sets;
+// when given, the wait first waits up to stall_cycles for it, runs out and
+// reports failure as an expired wait would.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* stall = nullptr,
+                                          long long stall_cycles = 0) {
   const long long t0 = clock64();
+  if (stall != nullptr) {
+    while (*stall == 0) {
+      if (clock64() - t0 > stall_cycles) return false;
+    }
+  }
   while (!mbar_test(bar, parity)) {
     if (clock64() - t0 > (1ll << 31)) return false;
   }
@@ -143,7 +152,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gram(const float* __restrict__ A, int ma, const float* __restrict__ B, int mb, long long K, int g5b,
-              double2* __restrict__ partial, int* __restrict__ err, int nraw) {
+              double2* __restrict__ partial, int* __restrict__ err, int nraw, const int* stall,
+              long long stall_cycles) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* stage_base = smem;
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + 2 * kStage);  // [0], [1]: stages
@@ -201,7 +211,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   auto flush = [&]() {
     // all MMAs issued so far are complete once the last commit's phase is
     if (last_stage >= 0) {
-      const bool ok = mbar_wait(smem_u32(&bars[last_stage]), last_parity);
+      const bool ok = mbar_wait(smem_u32(&bars[last_stage]), last_parity, stall, stall_cycles);
       if (__syncthreads_or(!ok)) failed = true;
     }
     tc_fence_after();
@@ -232,7 +242,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     else if (nraw == 2) cp_async_wait<1>();
     else cp_async_wait<0>();
     bool ok = true;
-    if (use >= 1) ok = mbar_wait(smem_u32(&bars[stage]), (use - 1) & 1);  // stage free again
+    if (use >= 1) ok = mbar_wait(smem_u32(&bars[stage]), (use - 1) & 1, stall, stall_cycles);  // stage free again
     if (__syncthreads_or(!ok)) {  // also makes every thread's raw copies visible
       failed = true;
       break;
@@ -304,7 +314,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (!failed) flush();
   if (failed) {
     if (tid == 0) atomicExch(err, 1);
-    // bounded wait for this CTA's own MMAs before releasing tensor memory
+    // bounded wait (no stall) for this CTA's own MMAs before releasing tensor memory
     if (last_stage >= 0) mbar_wait(smem_u32(&bars[last_stage]), last_parity);
   }
   if (!failed && warp < 4) {
@@ -327,14 +337,14 @@ int tc_gram_max_rows() { return kTcM; }
 int tc_gram_max_rhs() { return kTcN / 2; }
 
 cudaError_t launch_tc_gram(const void* A, int ma, const void* B, int mb, int64_t V, int g5b, double2* partial,
-                           int nblk, int* err, cudaStream_t st) {
+                           int nblk, int* err, const int* stall, long long stall_cycles, cudaStream_t st) {
   if (ma < 1 || ma > kTcM || mb < 1 || 2 * mb > kTcN) return cudaErrorInvalidValue;
   const uint32_t nraw = raw_stages(ma + mb);
   const uint32_t smem = 2 * kStage + kCtrl + nraw * (uint32_t)(ma + mb) * kRawPitch;
   cudaError_t e = cudaFuncSetAttribute(k_tc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_tc_gram<<<nblk, kTcThreads, smem, st>>>(static_cast<const float*>(A), ma, static_cast<const float*>(B), mb,
-                                            24LL * V, g5b, partial, err, (int)nraw);
+                                            24LL * V, g5b, partial, err, (int)nraw, stall, stall_cycles);
   return cudaGetLastError();
 }
 

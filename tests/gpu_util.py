@@ -20,3 +20,15 @@ def host(t):
 
 def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def site_rel(got, want):
+    """Largest error of one site (over sites and right-hand sides), relative to
+    the RMS site norm of want: |got(s) - want(s)| / rms_s |want(s)|.  Unlike the
+    whole-field norm it is not diluted when an error is confined to a few
+    sites (a boundary plane, a tail block)."""
+    g = np.asarray(got).reshape(-1, 12)
+    w = np.asarray(want).reshape(-1, 12)
+    err = np.linalg.norm(g - w, axis=1)
+    rms = np.sqrt(np.mean(np.sum(np.abs(w) ** 2, axis=1)))
+    return float(err.max() / rms)

@@ -118,11 +118,14 @@ def _prototypes():
 
 
 def _kind(decl):
-    """'p' for a pointer parameter (including arrays), 'd' for double, 'i' for int / enum."""
+    """'p' for a pointer parameter (including arrays), 'd' for double, 'l' for
+    long long, 'i' for int / enum."""
     if "*" in decl or "[" in decl:
         return "p"
     if re.search(r"\bdouble\b", decl):
         return "d"
+    if re.search(r"\blong\s+long\b", decl):
+        return "l"
     return "i"
 
 
@@ -131,6 +134,8 @@ def _ctype_kind(t):
         return "p"
     if t is ctypes.c_double:
         return "d"
+    if t is ctypes.c_longlong:
+        return "l"
     return "i"
 
 

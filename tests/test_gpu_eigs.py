@@ -50,3 +50,23 @@ def test_eigs_fp32_8x8_residuals():
         assert np.linalg.norm(r) < 5e-5 * lmax
     gram = np.einsum("ia,ja->ij", ev.reshape(n_ev, -1).conj(), ev.reshape(n_ev, -1))
     assert np.max(np.abs(gram - np.eye(n_ev))) < 1e-5
+
+
+def test_eigs_block_wider_than_one_gram_tile():
+    """30 pairs: a block of 75 vectors, so every Gram matrix of the iteration is
+    assembled from 64-vector tiles (4^4, FP64, against dense eigh)."""
+    prob = small_problem()
+    n_ev = 30
+    evecs = torch.zeros((n_ev,) + field_shape(prob["dims"]), dtype=torch.complex128, device="cuda")
+    with Ctx(prob["dims"], dev(prob["links"]), "fp64") as c:
+        evals, lmax = ov_eigs(c.handle, n_ev, 1e-10, 600, evecs)
+    ev = host(evecs).reshape(n_ev, -1)
+    w = prob["w_all"]
+    # the 30 smallest |lambda|; a degenerate pair may straddle the cut, so compare |lambda|
+    assert np.max(np.abs(np.abs(evals) - np.abs(w[:n_ev]))) < 1e-8
+    for i in range(n_ev):
+        r = wilson.kernel_k(prob["links"], ev[i].reshape(field_shape(prob["dims"]))) - evals[i] * ev[i].reshape(
+            field_shape(prob["dims"]))
+        assert np.linalg.norm(r) < 1e-8
+    gram = ev.conj() @ ev.T
+    assert np.max(np.abs(gram - np.eye(n_ev))) < 1e-9

@@ -1,15 +1,16 @@
-"""GMRESR with the FP32 GCR level of a 16-bit context
-(ov_enable_fp32_operator) against the FP64 oracle on 4^4 with 8 deflated
-pairs: same solution (dense solve of the polynomial operator, the oracle's
-residual), no more FP64 passes than without it, whether the FP32 copy is
-made before or after the sign configuration; a no-op on FP32 contexts.
-(Named to run after the other GPU tests.)"""
+"""GMRESR with the FP32 GCR level of a 16-bit context against the FP64 oracle
+on 4^4 with 8 deflated pairs: same solution (dense solve of the polynomial
+operator, the oracle's residual), no more FP64 passes than GCR in the
+storage precision (ov_set_gmresr_fp32_level off), whether the FP32 copy is
+made by ov_enable_fp32_operator before or after the sign configuration or by
+the solver itself on its first call (the default); a no-op on FP32 contexts.
+Every case builds its own contexts, so the tests depend on no other test."""
 import numpy as np
 import pytest
 
 from oracle import chebyshev, dense, overlap
 from paper_1510_06897_gb300 import inputs
-from paper_1510_06897_gb300.binding import Ctx, ov_enable_fp32_operator
+from paper_1510_06897_gb300.binding import Ctx, ov_enable_fp32_operator, ov_set_gmresr_fp32_level
 from tests.gpu_util import dev, host, need_gpu
 from tests.oracle_fixtures import small_problem
 
@@ -36,12 +37,14 @@ def problem():
     return prob, cfg, dmat
 
 
-def _solve(prob, b, prec, fp32_level, enable_first=True):
+def _solve(prob, b, prec, fp32_level, enable_first=True, automatic=False):
     with Ctx(prob["dims"], dev(prob["links"]), prec) as c:
-        if fp32_level and enable_first:
+        if not fp32_level:
+            ov_set_gmresr_fp32_level(c.handle, 0)
+        elif enable_first and not automatic:
             ov_enable_fp32_operator(c.handle, dev(prob["links"]))
         c.sign_config(ORDER, prob["a"], prob["b"], prob["evals"], dev(prob["evecs"]))
-        if fp32_level and not enable_first:
+        if fp32_level and not enable_first and not automatic:
             ov_enable_fp32_operator(c.handle, prob["links"])  # host links
         x, it, res = c.solve_gmresr(dev(b), MU)
         return host(x), res, c.stats()
@@ -63,6 +66,21 @@ def test_gmresr_fp32_gcr_level(problem, prec, enable_first):
         assert np.linalg.norm(rr) <= 2e-10 * np.linalg.norm(b[r]), r
         want = np.linalg.solve(dmat, b[r].ravel())
         assert np.linalg.norm(x[r].ravel() - want) <= 1e-8 * np.linalg.norm(want), r
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_fp32_level_is_the_default(problem, prec):
+    """Without any call, the solver builds the FP32 copy from the context's own
+    FP64 links: the result equals, bit for bit, that of a context given the
+    FP32 copy by ov_enable_fp32_operator (4^4: no stencil tuning, so both
+    contexts run the same launch shapes)."""
+    prob, _, _ = problem
+    b = inputs.gaussian_source(prob["dims"], seed=9510, nrhs=2)
+    x_auto, res_auto, st_auto = _solve(prob, b, prec, True, automatic=True)
+    x_exp, res_exp, st_exp = _solve(prob, b, prec, True)
+    assert res_auto <= 1e-10
+    assert st_auto["outer_iterations"] == st_exp["outer_iterations"]
+    assert np.array_equal(x_auto, x_exp)
 
 
 def test_fp32_operator_is_a_no_op_on_fp32_contexts(problem):

@@ -14,13 +14,18 @@ import pytest
 from oracle import chebyshev, overlap, wilson
 from paper_1510_06897_gb300 import inputs
 from paper_1510_06897_gb300.binding import Ctx, OverlapError
-from tests.gpu_util import dev, host, need_gpu, rel, torch
+from tests.gpu_util import dev, host, need_gpu, rel, site_rel, torch
 from tests.oracle_fixtures import field_shape, small_problem
 
 pytestmark = pytest.mark.gpu
 
 STENCIL_TOL = {"fp64": 1e-13, "fp32": 1e-6, "fp16": 2e-3, "bf16": 1.5e-2}
 SIGN_TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp16": 1e-2, "bf16": 6e-2}
+# largest single-site error over the RMS site norm (site_rel): a site's output
+# mixes its 9 operands with ~unit weights, so a 16-bit site error stays within
+# a few storage roundings; 2.5 x the field bound leaves room for the extreme
+# site of a Gaussian field and still fails on an error local to a plane
+SITE_FACTOR = 2.5
 
 
 @pytest.fixture(autouse=True)
@@ -41,6 +46,8 @@ def test_wilson_and_kernel(prec, dims, antiperiodic):
     want_k = np.stack([wilson.kernel_k(links, p, antiperiodic_t=antiperiodic) for p in psi])
     assert rel(got_w, want_w) < STENCIL_TOL[prec]
     assert rel(got_k, want_k) < STENCIL_TOL[prec]
+    assert site_rel(got_w, want_w) < SITE_FACTOR * STENCIL_TOL[prec]
+    assert site_rel(got_k, want_k) < SITE_FACTOR * STENCIL_TOL[prec]
 
 
 def test_wilson_complex64_and_host_pointers():
@@ -79,9 +86,9 @@ def test_sign_overlap_4x4(prec):
         got_d = host(c.overlap(dev(psi), mu))
         got_dd = host(c.overlap(dev(psi), mu, dagger=True))
     print(prec, rel(got_s, want_s), rel(got_d, want_d), rel(got_dd, want_dd))
-    assert rel(got_s, want_s) < SIGN_TOL[prec]
-    assert rel(got_d, want_d) < SIGN_TOL[prec]
-    assert rel(got_dd, want_dd) < SIGN_TOL[prec]
+    for got, want in ((got_s, want_s), (got_d, want_d), (got_dd, want_dd)):
+        assert rel(got, want) < SIGN_TOL[prec]
+        assert site_rel(got, want) < SITE_FACTOR * SIGN_TOL[prec]
 
 
 @pytest.mark.parametrize("order", [1, 2, 7])
