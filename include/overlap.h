@@ -79,7 +79,8 @@ typedef struct {
   long long kernel_launches;   /* all kernels launched by this context */
   long long dslash_launches;   /* stencil kernels (one K or D_W application each, all RHS) */
   long long sign_applies;      /* sign(K) applications (per RHS) */
-  long long inner_iterations;  /* CG (SUMR) iterations in the context's precision (last solve) */
+  long long inner_iterations;  /* CG (SUMR) iterations in the context's precision (last solve);
+                                  filter + Rayleigh-Ritz steps of the last ov_eigs */
   long long outer_iterations;  /* FP64 defect-correction steps (last ov_solve) */
   long long dslash_timed;      /* stencil launches timed while profiling was on */
   double dslash_ms;            /* their summed device time (CUDA events on the context stream) */
@@ -260,7 +261,7 @@ ov_status ov_set_gmresr_params(ov_ctx* ctx, int inner_order, double inner_tol, i
  * doubles, ascending |lambda|; evecs: complex128 [n_ev][V][4][3] (host or
  * device).  tol: relative eigen-residual ||K phi - lambda phi|| <= tol * lambda_max.
  * lambda_max_out (may be NULL): an upper bound of |lambda| of K.  max_iter
- * counts filter + Rayleigh-Ritz steps (filter degree 32 on K^2; the
+ * counts filter + Rayleigh-Ritz steps (filter degree 96 on K^2; the
  * environment variable OV_EIGS_DEGREE overrides it, 4 .. 256) on a block of
  * max(n_ev + 8, 2.5 n_ev) vectors, at most 128 (so n_ev <= 120).
  * Errors: OV_ERR_INVALID, OV_ERR_NOT_CONVERGED (best pairs returned; also when

@@ -199,7 +199,10 @@ ov_status autotune(ov_ctx* c, Inst& I, const void* links_dev) {
 
 // Stencil shape for nrhs right-hand sides: tuned on first use (threads per
 // block, register cap, right-hand sides per thread; link layout as tuned at
-// create) and cached per nrhs.
+// create) and cached per nrhs.  The candidates are timed on at most
+// kTuneRhs right-hand sides (one launch of every candidate on all 102 vectors
+// of an eigensolver block would cost seconds), which ranks the shapes alike.
+constexpr int kTuneRhs = 12;
 ov_status batch_cfg(ov_ctx* c, Inst& I, int nrhs, DslashCfg* out) {
   if (nrhs <= 1) {
     *out = I.cfg;
@@ -222,10 +225,11 @@ ov_status batch_cfg(ov_ctx* c, Inst& I, int nrhs, DslashCfg* out) {
     }
   } else if (c->g.V >= 4096) {
     const int64_t V = c->g.V;
+    const int nt = std::min(nrhs, kTuneRhs);  // right-hand sides the candidates are timed on
     DevBuf buf[4];
     for (DevBuf& b : buf) {
-      OV_CK(b.ensure(I.pbytes(V) * nrhs));
-      OV_CK(cudaMemsetAsync(b.p, 0, I.pbytes(V) * nrhs, c->st));
+      OV_CK(b.ensure(I.pbytes(V) * nt));
+      OV_CK(cudaMemsetAsync(b.p, 0, I.pbytes(V) * nt, c->st));
     }
     cudaEvent_t e0, e1;
     OV_CK(cudaEventCreate(&e0));
@@ -234,13 +238,13 @@ ov_status batch_cfg(ov_ctx* c, Inst& I, int nrhs, DslashCfg* out) {
     for (int tpb : {64, 96, 128, 192, 256})
       for (const auto& v : kVariants)
         for (int bk : {0, 1}) {
-          if (v[1] > nrhs || (I.p == OP_F64 && v[1] != 1) || (bk && !brick_lattice_ok(c->g, tpb)) ||
+          if (v[1] > nt || (I.p == OP_F64 && v[1] != 1) || (bk && !brick_lattice_ok(c->g, tpb)) ||
               (v[0] >= 5 && tpb > 64))
             continue;
           DslashCfg cfg{tpb, v[0], I.cfg.lrec, v[1]};
           cfg.brick = bk;
           float ms = 0.f;
-          OV_TRY(time_variant(c, I, cfg, I.links.p, nrhs, buf, e0, e1, &ms));
+          OV_TRY(time_variant(c, I, cfg, I.links.p, nt, buf, e0, e1, &ms));
           if (ms < best) {
             best = ms;
             best_cfg = cfg;
@@ -256,7 +260,7 @@ ov_status batch_cfg(ov_ctx* c, Inst& I, int nrhs, DslashCfg* out) {
               cfg.async = as;
               cfg.brick = bk;
               float ms = 0.f;
-              OV_TRY(time_variant(c, I, cfg, I.links.p, nrhs, buf, e0, e1, &ms));
+              OV_TRY(time_variant(c, I, cfg, I.links.p, nt, buf, e0, e1, &ms));
               if (ms < best) {
                 best = ms;
                 best_cfg = cfg;
@@ -266,7 +270,7 @@ ov_status batch_cfg(ov_ctx* c, Inst& I, int nrhs, DslashCfg* out) {
     DslashCfg sc;
     if (I.cfg.lrec == 12 && slab_cfg(c, I, &sc)) {
       float ms = 0.f;
-      OV_TRY(time_variant(c, I, sc, I.links.p, nrhs, buf, e0, e1, &ms));
+      OV_TRY(time_variant(c, I, sc, I.links.p, nt, buf, e0, e1, &ms));
       if (ms < best) {
         best = ms;
         best_cfg = sc;
