@@ -822,10 +822,13 @@ def solve_16_timing():
 
 def gradient_timing():
     """Adjoint of chi^dagger P(K) chi at 16^3 x 32, order 128, complex64 chi, FP32
-    context: time of ov_sign_poly_grad against one forward P(K) chi apply."""
+    context: time of ov_sign_poly_grad against one forward P(K) chi apply, with
+    every recurrence term kept on the device (the default) and with
+    checkpoints every 16 terms and recomputation (allowance 0)."""
     import torch
     from paper_1510_06897_gb300 import inputs
-    from paper_1510_06897_gb300.binding import Ctx, ov_sign_apply, ov_sign_poly_grad
+    from paper_1510_06897_gb300.binding import (Ctx, ov_get_stats, ov_set_grad_memory, ov_sign_apply,
+                                                ov_sign_poly_grad)
     dims = (16, 16, 16, 32)
     links = torch.from_numpy(inputs.gauge_links(dims, seed=1005)).cuda()
     chi = torch.from_numpy(inputs.gaussian_source(dims, seed=2005).astype(np.complex64)).cuda()
@@ -842,13 +845,22 @@ def gradient_timing():
             ov_sign_apply(c.handle, chi, out, 1)
         torch.cuda.synchronize()
         t_fwd = (time.perf_counter() - t0) / 3
-        t0 = time.perf_counter()
-        for _ in range(3):
+        t_grad = {}
+        for name, allowance in (("kept", -1), ("recompute", 0)):
+            ov_set_grad_memory(c.handle, allowance)
             ov_sign_poly_grad(c.handle, order, a, b, chi, grad)
-        torch.cuda.synchronize()
-        t_grad = (time.perf_counter() - t0) / 3
-    return {"lattice": "16x16x16x32", "order": order, "forward_ms": t_fwd * 1e3, "gradient_ms": t_grad * 1e3,
-            "ratio": t_grad / t_fwd}
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(3):
+                ov_sign_poly_grad(c.handle, order, a, b, chi, grad)
+            torch.cuda.synchronize()
+            t_grad[name] = ((time.perf_counter() - t0) / 3, ov_get_stats(c.handle)["grad_kept_terms"])
+        ov_set_grad_memory(c.handle, -1)
+    return {"lattice": "16x16x16x32", "order": order, "forward_ms": t_fwd * 1e3,
+            "gradient_ms": t_grad["kept"][0] * 1e3, "ratio": t_grad["kept"][0] / t_fwd,
+            "kept_terms": t_grad["kept"][1],
+            "recompute": {"gradient_ms": t_grad["recompute"][0] * 1e3, "ratio": t_grad["recompute"][0] / t_fwd,
+                          "kept_terms": t_grad["recompute"][1]}}
 
 
 if __name__ == "__main__":

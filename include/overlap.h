@@ -99,6 +99,9 @@ typedef struct {
                                   copies, double-buffered; 0: loads straight into registers */
   int stencil_brick;           /* 1: its blocks cover 8 x 4 x (stencil_tpb / 32) bricks of sites;
                                   0: consecutive sites of one (x, y) plane */
+  int grad_kept_terms;         /* vectors of the recurrence the last ov_sign_poly_grad kept on the device:
+                                  2N + 1 (every b_k and K b_{k+1}, nothing recomputed) or its
+                                  checkpoints (b_k for k = 1, 2 mod 16) */
 } ov_stats;
 
 /* Creates a context for one lattice and gauge field (Eq. 2 links).  Copies and
@@ -286,10 +289,25 @@ ov_status ov_sign_poly_quad(ov_ctx* ctx, int order, double lo, double hi, const 
  * polynomial of Eq. 3 on [lo^2, hi^2], with respect to every link:
  * grad_links complex128 [4][V][3][3] receives F_mu(x) in su(3) with
  * dS/deps = sum Re tr(X^dagger F) for U -> exp(eps X) U.  chi: one spinor in
- * `dtype`.  Runs the recurrence forward with checkpoints every 16 terms, then
- * backward with recomputation.  Errors: OV_ERR_INVALID. */
+ * `dtype`.  Runs the Clenshaw recurrence forward, then the adjoint recurrence
+ * backward.  When the 2N + 1 vectors b_k and K b_{k+1} of the forward sweep
+ * fit in the allowance of ov_set_grad_memory they all stay on the device
+ * (4N + 3 stencil launches); otherwise only b_k for k = 1, 2 mod 16 are kept
+ * and the backward sweep recomputes the rest (about 6N launches).
+ * ov_stats.grad_kept_terms says which.  Errors: OV_ERR_INVALID, OV_ERR_NOMEM,
+ * OV_ERR_CUDA. */
 ov_status ov_sign_poly_grad(ov_ctx* ctx, int order, double lo, double hi, const void* chi, void* grad_links,
                             ov_dtype dtype);
+
+/* Device memory ov_sign_poly_grad may fill with the terms of the forward
+ * recurrence so that it recomputes none: bytes >= 0 sets that allowance
+ * (0: always checkpoint and recompute); bytes < 0 (the default) uses half the
+ * device memory free at the start of each call (counting what the context
+ * already holds for it).  ov_sign_poly_quad and ov_sign_poly_grad keep their
+ * device vectors in the context between calls, so that repeated calls
+ * allocate nothing; this call (with any value) and ov_destroy release them.
+ * Errors: OV_ERR_INVALID (null ctx), OV_ERR_CUDA. */
+ov_status ov_set_grad_memory(ov_ctx* ctx, long long bytes);
 
 /* Profiling of the stencil kernel with CUDA events on the context stream;
  * device time is added to ov_stats.dslash_ms and the number of stencil

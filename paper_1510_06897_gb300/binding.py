@@ -49,7 +49,8 @@ class ov_stats(ctypes.Structure):
                 ("gcr_iterations", ctypes.c_longlong),
                 ("gmresr_order", ctypes.c_int),
                 ("stencil_async", ctypes.c_int),
-                ("stencil_brick", ctypes.c_int)]
+                ("stencil_brick", ctypes.c_int),
+                ("grad_kept_terms", ctypes.c_int)]
 
 
 _LIB = None
@@ -82,6 +83,7 @@ _SIGNATURES = {
     "ov_get_residual_history": [_vp, ctypes.POINTER(_d), _i, ctypes.POINTER(_i)],
     "ov_set_gmresr_fp32_level": [_vp, _i],
     "ov_test_wait_expiry": [_vp, ctypes.c_longlong],
+    "ov_set_grad_memory": [_vp, ctypes.c_longlong],
     "ov_sign_poly_quad": [_vp, _i, _d, _d, _vp, _vp, _i, ctypes.POINTER(_d)],
     "ov_wilson_noalloc": [ctypes.POINTER(_i), _vp, _vp, _vp, _i, _i, _i, _vp],
     "ov_stout_smear": [ctypes.POINTER(_i), _vp, _vp, _d, _d, _i, _vp],
@@ -242,6 +244,11 @@ def ov_enable_fp32_operator(ctx, links):
 def ov_set_gmresr_fp32_level(ctx, on=True):
     """GCR level of GMRESR on an FP32 copy of a 16-bit operator (default) or not."""
     return _check(lib().ov_set_gmresr_fp32_level(ctx, int(bool(on))), ctx)
+
+
+def ov_set_grad_memory(ctx, nbytes=-1):
+    """Device bytes ov_sign_poly_grad may fill with recurrence terms (< 0: half the free memory; 0: recompute)."""
+    return _check(lib().ov_set_grad_memory(ctx, int(nbytes)), ctx)
 
 
 def ov_set_gmresr_params(ctx, inner_order=0, inner_tol=0.1, inner_maxit=1000, max_dirs=12):

@@ -116,6 +116,7 @@ ov_status ov_destroy(ov_ctx* c) {
   c->hi.release();
   c->lo.release();
   c->mid.release();
+  c->gw.release();
   for (cudaEvent_t ev : c->evs) cudaEventDestroy(ev);
   for (DevBuf* b : {&c->d_sgn, &c->d_c, &c->d_partial, &c->d_scalars, &c->d_gram, &c->d_err, &c->d_never, &c->stage_in, &c->stage_out, &c->stage_links,
                     &c->o_x, &c->o_r, &c->o_rhs, &c->o_q})

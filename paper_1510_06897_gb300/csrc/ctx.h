@@ -33,6 +33,16 @@ struct DevBuf {
   char* c() const { return static_cast<char*>(p); }
 };
 
+// Device vectors of ov_sign_poly_quad / ov_sign_poly_grad, kept between calls
+// so that repeated gradients (one per molecular-dynamics step) allocate
+// nothing; ov_set_grad_memory and ov_destroy release them.
+struct GradWork {
+  DevBuf xchi, rot, ck, segb, segt, bbar, tbar, gvec, gbar, zero, t, G, keep;
+  void release() {
+    for (DevBuf* b : {&xchi, &rot, &ck, &segb, &segt, &bbar, &tbar, &gvec, &gbar, &zero, &t, &G, &keep}) b->release();
+  }
+};
+
 // One operator instance: links, eigenvectors and work vectors in one precision.
 struct Inst {
   OpPrec p = OP_F64;   // link / recurrence storage
@@ -107,6 +117,10 @@ struct ov_ctx {
   // GCR level of GMRESR on an FP32 copy of the operator for 16-bit contexts
   // (built from the FP64 links on first use unless switched off)
   bool gm_fp32 = true;
+  // gradient (ov_set_grad_memory): device bytes the recurrence terms may
+  // occupy so that none is recomputed; < 0: half the free memory at the call
+  long long grad_mem = -1;
+  GradWork gw;
   std::vector<double> coef_relaxed;
   double relaxed_key[4] = {0, 0, 0, 0};
   ov_stats stats{};

@@ -114,6 +114,222 @@ __global__ void __launch_bounds__(128) k_force_pairs(Lattice g, const void* __re
   }
 }
 
+template <int N>
+__device__ __forceinline__ void cp_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// cp.async of pair p's u and v over the box and faces into stage p % NS:
+// 16-byte chunks, consecutive threads on consecutive slots of one chunk
+template <class T, class TG, class R>
+__device__ __forceinline__ void force_tile_issue(const Lattice& g, unsigned char* sm, const int* ext,
+                                                 const PairArgsDev<R>& P, int p) {
+  const uint32_t base = (uint32_t)__cvta_generic_to_shared(sm + (p % TG::NS) * TG::STAGE);
+  for (int idx = threadIdx.x; idx < 2 * TG::CH * TG::NE; idx += 4 * TG::NB) {
+    const int e = idx % TG::NE, r = idx / TG::NE;  // r = which * CH + chunk
+    const int which = r / TG::CH, ch = r % TG::CH;
+    const char* src = (which ? P.v[p] : P.u[p]) + ((int64_t)ch * g.V + ext[e]) * 16;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(base + (uint32_t)(r * TG::NE + e) * 16u),
+                 "l"(src)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Shared-memory tiled form of the same sums.  A block covers a
+// BX x BY x BZ x BT box of sites and thread (mu, i) the link (box site i, mu).
+// For every pair, u and v over the box and its +x, +y, +z, +t faces are
+// copied into shared memory once with cp.async, three stages deep (pairs
+// p + 1 and p + 2 land while pair p is used; one barrier per pair), so each
+// vector leaves L2 about
+// (box + faces) / box times (2.25 for 4 x 4 x 4 x 2) instead of once for the
+// site and once more for every direction that reaches it from outside the
+// block.  The pairs are folded in the same order with the same arithmetic as
+// k_force_pairs.
+template <class T, int BX, int BY, int BZ, int BT>
+struct ForceTile {
+  static constexpr int NB = BX * BY * BZ * BT;  // box sites; threads = 4 NB
+  static constexpr int H0 = BY * BZ * BT, H1 = BX * BZ * BT, H2 = BX * BY * BT, H3 = BX * BY * BZ;
+  static constexpr int NE = NB + H0 + H1 + H2 + H3;  // box + faces
+  static constexpr int CH = std::is_same<T, F64>::value ? 12 : 6;  // 16-byte chunks per site
+  static constexpr int STAGE = 2 * CH * NE * 16;                 // u and v of one pair
+  static constexpr int NS = 3;                                   // stages
+  static constexpr int SMEM = NS * STAGE + NE * 4;               // stages + site table
+  static bool fits(const LatticeH& g) {
+    return g.L[0] % BX == 0 && g.L[1] % BY == 0 && g.L[2] % BZ == 0 && g.L[3] % BT == 0;
+  }
+};
+
+// spinor of slot e of vector `which` (0: u, 1: v) of one stage
+template <class T, class R, int NE, int CH>
+__device__ __forceinline__ void smem_spinor(const unsigned char* stage, int which, int e, Spinor<R>& o) {
+  if constexpr (CH == 12) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      const double2 v = *reinterpret_cast<const double2*>(stage + ((which * CH + c) * NE + e) * 16);
+      o.c[c] = {R(v.x), R(v.y)};
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const float4 v = *reinterpret_cast<const float4*>(stage + ((which * CH + c) * NE + e) * 16);
+      o.c[2 * c] = {R(v.x), R(v.y)};
+      o.c[2 * c + 1] = {R(v.z), R(v.w)};
+    }
+  }
+}
+
+// one pair's contribution to A and B of link (box site i, MU); nb: slot of i + MU
+template <int MU, class T, class R, class TG>
+__device__ __forceinline__ void force_tile_pair(const unsigned char* st, int i, int nb, R w, cplx<R> (&A)[9],
+                                                cplx<R> (&B)[9]) {
+  Spinor<R> x;
+  Half<R> hv, ha;
+  // A += w v(x+mu) [(1 - g_mu) g5 u(x)]^dagger
+  smem_spinor<T, R, TG::NE, TG::CH>(st, 0, i, x);
+#pragma unroll
+  for (int k = 6; k < 12; ++k) x.c[k] = R(-1) * x.c[k];
+  project<MU, -1>(x, ha);
+  smem_spinor<T, R, TG::NE, TG::CH>(st, 1, nb, x);
+  project<MU, -1>(x, hv);
+  scale_half(hv, w);
+  outer_acc2(A, hv, ha);
+  // B += w v(x) [(1 + g_mu) g5 u(x+mu)]^dagger
+  smem_spinor<T, R, TG::NE, TG::CH>(st, 0, nb, x);
+#pragma unroll
+  for (int k = 6; k < 12; ++k) x.c[k] = R(-1) * x.c[k];
+  project<MU, +1>(x, ha);
+  smem_spinor<T, R, TG::NE, TG::CH>(st, 1, i, x);
+  project<MU, +1>(x, hv);
+  scale_half(hv, w);
+  outer_acc2(B, hv, ha);
+}
+
+// G_MU(s) += sg (-1/2 U A + 1/2 B U^dagger)
+template <int MU, class T, class R>
+__device__ __forceinline__ void force_tile_store(const Lattice& g, const void* links, int64_t s, R sg,
+                                                 const cplx<R> (&A)[9], const cplx<R> (&B)[9], cplx<R>* G) {
+  const int64_t V = g.V;
+  SU3<R> U;
+  load_link<T, R>(links, MU, s, V, U);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      cplx<R> ua = {R(0), R(0)}, bu = {R(0), R(0)};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        ua = ua + cmul(U.u[3 * a + k], A[3 * k + b]);
+        bu = bu + cmul(B[3 * a + k], conj(U.u[3 * b + k]));
+      }
+      cplx<R>* gp = G + ((int64_t)(MU * 9 + 3 * a + b)) * V + s;
+      *gp = *gp + (sg * R(0.5)) * (bu - ua);
+    }
+}
+
+template <class T, int BX, int BY, int BZ, int BT>
+__global__ void __launch_bounds__(4 * BX * BY * BZ * BT, 1)
+    k_force_tile(Lattice g, const void* __restrict__ links, PairArgsDev<typename Store<T>::R> P, void* Gv) {
+  using R = typename Store<T>::R;
+  using TG = ForceTile<T, BX, BY, BZ, BT>;
+  extern __shared__ __align__(16) unsigned char fsm[];
+  int* ext = reinterpret_cast<int*>(fsm + TG::NS * TG::STAGE);
+  const int tid = threadIdx.x;
+  int b = blockIdx.x;
+  const int nbx = g.L[0] / BX, nby = g.L[1] / BY, nbz = g.L[2] / BZ;
+  const int X0 = (b % nbx) * BX;
+  b /= nbx;
+  const int Y0 = (b % nby) * BY;
+  b /= nby;
+  const int Z0 = (b % nbz) * BZ;
+  const int T0 = (b / nbz) * BT;
+  // lattice site of every slot: box sites, then the +x, +y, +z, +t faces
+  for (int e = tid; e < TG::NE; e += 4 * TG::NB) {
+    int c[4];
+    if (e < TG::NB) {
+      c[0] = e % BX;
+      c[1] = (e / BX) % BY;
+      c[2] = (e / (BX * BY)) % BZ;
+      c[3] = e / (BX * BY * BZ);
+    } else if (e < TG::NB + TG::H0) {
+      const int f = e - TG::NB;
+      c[0] = BX;
+      c[1] = f % BY;
+      c[2] = (f / BY) % BZ;
+      c[3] = f / (BY * BZ);
+    } else if (e < TG::NB + TG::H0 + TG::H1) {
+      const int f = e - TG::NB - TG::H0;
+      c[0] = f % BX;
+      c[1] = BY;
+      c[2] = (f / BX) % BZ;
+      c[3] = f / (BX * BZ);
+    } else if (e < TG::NB + TG::H0 + TG::H1 + TG::H2) {
+      const int f = e - TG::NB - TG::H0 - TG::H1;
+      c[0] = f % BX;
+      c[1] = (f / BX) % BY;
+      c[2] = BZ;
+      c[3] = f / (BX * BY);
+    } else {
+      const int f = e - TG::NB - TG::H0 - TG::H1 - TG::H2;
+      c[0] = f % BX;
+      c[1] = (f / BX) % BY;
+      c[2] = f / (BX * BY);
+      c[3] = BT;
+    }
+    const int gx = (X0 + c[0]) % g.L[0], gy = (Y0 + c[1]) % g.L[1];
+    const int gz = (Z0 + c[2]) % g.L[2], gt = (T0 + c[3]) % g.L[3];
+    ext[e] = gx + g.L[0] * (gy + g.L[1] * (gz + g.L[2] * gt));
+  }
+  __syncthreads();
+  const int mu = tid / TG::NB, i = tid % TG::NB;  // mu is warp-uniform: NB is a multiple of 32
+  const int ix = i % BX, iy = (i / BX) % BY, iz = (i / (BX * BY)) % BZ, it = i / (BX * BY * BZ);
+  int nb;  // slot of site i + mu
+  if (mu == 0) nb = ix < BX - 1 ? i + 1 : TG::NB + (iy + BY * (iz + BZ * it));
+  else if (mu == 1) nb = iy < BY - 1 ? i + BX : TG::NB + TG::H0 + (ix + BX * (iz + BZ * it));
+  else if (mu == 2) nb = iz < BZ - 1 ? i + BX * BY : TG::NB + TG::H0 + TG::H1 + (ix + BX * (iy + BY * it));
+  else nb = it < BT - 1 ? i + BX * BY * BZ : TG::NB + TG::H0 + TG::H1 + TG::H2 + (ix + BX * (iy + BY * iz));
+  cplx<R> A[9], B[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) A[k] = B[k] = {R(0), R(0)};
+  static_assert(TG::NS == 3, "the waits below assume three stages");
+  if (P.n > 0) force_tile_issue<T, TG>(g, fsm, ext, P, 0);
+  if (P.n > 1) force_tile_issue<T, TG>(g, fsm, ext, P, 1);
+  for (int p = 0; p < P.n; ++p) {
+    // groups committed so far: pairs 0 .. min(p + 1, n - 1); pair p must be complete
+    if (p + 1 < P.n) cp_wait_group<1>();
+    else cp_wait_group<0>();
+    __syncthreads();  // every thread's copies of pair p have landed; pair p - 1 is used up
+    if (p + 2 < P.n) force_tile_issue<T, TG>(g, fsm, ext, P, p + 2);  // into the stage of pair p - 1
+    const unsigned char* st = fsm + (p % TG::NS) * TG::STAGE;
+    const R w = P.w[p];
+    switch (mu) {
+      case 0: force_tile_pair<0, T, R, TG>(st, i, nb, w, A, B); break;
+      case 1: force_tile_pair<1, T, R, TG>(st, i, nb, w, A, B); break;
+      case 2: force_tile_pair<2, T, R, TG>(st, i, nb, w, A, B); break;
+      default: force_tile_pair<3, T, R, TG>(st, i, nb, w, A, B); break;
+    }
+  }
+  cplx<R>* G = static_cast<cplx<R>*>(Gv);
+  const int64_t s = ext[i];
+  const R sg = (mu == 3 && g.antiperiodic_t && T0 + it == g.L[3] - 1) ? R(-1) : R(1);
+  switch (mu) {
+    case 0: force_tile_store<0, T, R>(g, links, s, sg, A, B, G); break;
+    case 1: force_tile_store<1, T, R>(g, links, s, sg, A, B, G); break;
+    case 2: force_tile_store<2, T, R>(g, links, s, sg, A, B, G); break;
+    default: force_tile_store<3, T, R>(g, links, s, sg, A, B, G); break;
+  }
+}
+
+template <class T, int BX, int BY, int BZ, int BT>
+void launch_force_tile(const Lattice& g, const void* links, const PairArgsDev<typename Store<T>::R>& P, void* G,
+                       cudaStream_t st) {
+  using TG = ForceTile<T, BX, BY, BZ, BT>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_force_tile<T, BX, BY, BZ, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TG::SMEM);
+    attr = true;
+  }
+  k_force_tile<T, BX, BY, BZ, BT><<<(unsigned)(g.V / TG::NB), 4 * TG::NB, TG::SMEM, st>>>(g, links, P, G);
+}
+
 void launch_force_pairs(OpPrec p, const LatticeH& gh, const void* links, const ForcePairs& pairs, void* G,
                         cudaStream_t st) {
   Lattice g;
@@ -132,11 +348,13 @@ void launch_force_pairs(OpPrec p, const LatticeH& gh, const void* links, const F
   if (p == OP_F64) {
     PairArgsDev<double> P;
     args(&P);
-    k_force_pairs<F64><<<grid, 128, 0, st>>>(g, links, P, G);
+    if (ForceTile<F64, 4, 4, 2, 2>::fits(gh)) launch_force_tile<F64, 4, 4, 2, 2>(g, links, P, G, st);
+    else k_force_pairs<F64><<<grid, 128, 0, st>>>(g, links, P, G);
   } else {
     PairArgsDev<float> P;
     args(&P);
-    k_force_pairs<F32><<<grid, 128, 0, st>>>(g, links, P, G);
+    if (ForceTile<F32, 4, 4, 4, 2>::fits(gh)) launch_force_tile<F32, 4, 4, 4, 2>(g, links, P, G, st);
+    else k_force_pairs<F32><<<grid, 128, 0, st>>>(g, links, P, G);
   }
 }
 

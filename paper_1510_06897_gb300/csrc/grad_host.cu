@@ -11,9 +11,14 @@
 //   dZ = alpha (dK K + K dK),
 // so each step k contributes the dK pairs (bbar_k, K b_{k+1}) and
 // (K bbar_k, b_{k+1}) with weight 2 alpha.  The adjoint runs upward in k
-// while the recurrence produced b_k downward, so b_{k+1} and K b_{k+1} are
-// recomputed 16 at a time from the checkpoints, and each segment's 32 pairs
-// are folded into the link accumulator by one force launch.
+// while the recurrence produced b_k downward.  When the 2N + 1 vectors b_k
+// and K b_{k+1} fit in the context's gradient memory allowance (by default
+// half the free device memory) the forward sweep writes every one of them to
+// its own slot and nothing is recomputed (4N + 3 stencil launches in all);
+// otherwise it keeps b_k for k = 1, 2 mod 16 and the reverse sweep recomputes
+// b_{k+1} and K b_{k+1} 16 at a time from those checkpoints (6N + ...).
+// Either way each segment of 16 adjoint steps folds its 32 pairs into the
+// link accumulator with one force launch.
 #include "ctx.h"
 
 using namespace ov;
@@ -22,12 +27,13 @@ namespace {
 constexpr int kSeg = 16;
 
 // Forward Clenshaw sweep b_k = c_k chi + 2 Z b_{k+1} - b_{k+2}, k = N .. 0
-// (b_{N+1} = b_{N+2} = 0), Z = alpha K^2 + beta: b_k lands in rot[k % 3],
-// t receives K b_{k+1}, and keep(k, b_k) sees every b_k as it is made.
-// Returns b_0 and b_2 (b_2 = zero when N < 2).
-template <class Keep>
+// (b_{N+1} = b_{N+2} = 0), Z = alpha K^2 + beta: b_k lands in out_of(k)
+// (which must not alias b_{k+1} or b_{k+2}), K b_{k+1} in t_of(k), and
+// keep(k, b_k) sees every b_k as it is made.  Returns b_0 and b_2 (b_2 =
+// zero when N < 2).
+template <class Out, class Tmp, class Keep>
 ov_status clenshaw_forward(ov_ctx* c, Inst& I, const std::vector<double>& cf, double alpha, double beta,
-                           const void* xchi, const void* zero, void* const rot[3], void* t, void** b0, const void** b2,
+                           const void* xchi, const void* zero, Out&& out_of, Tmp&& t_of, void** b0, const void** b2,
                            Keep&& keep) {
   const int N = (int)cf.size() - 1;
   EpiArgs ek;
@@ -36,7 +42,8 @@ ov_status clenshaw_forward(ov_ctx* c, Inst& I, const std::vector<double>& cf, do
   const void* bk2 = zero;  // b_{k+2}
   *b2 = zero;
   for (int k = N; k >= 0; --k) {
-    void* out = rot[k % 3];
+    void* out = out_of(k);
+    void* t = t_of(k);
     OV_TRY(k_step(c, I, bk1, t, 1, ek));
     EpiArgs e;
     e.m_w = c->m_w;
@@ -82,7 +89,8 @@ extern "C" ov_status ov_sign_poly_quad(ov_ctx* c, int order, double lo, double h
   const std::vector<double> cf = chebyshev_coefficients(order, lo, hi);
   const double a2 = lo * lo, b2 = hi * hi;
   const double alpha = 2.0 / (b2 - a2), beta = -(b2 + a2) / (b2 - a2);
-  DevBuf xchi, rot3, t, zero, gvec, gbar;
+  GradWork& w = c->gw;
+  DevBuf &xchi = w.xchi, &rot3 = w.rot, &t = w.t, &zero = w.zero, &gvec = w.gvec, &gbar = w.gbar;
   OV_CK(xchi.ensure(vb));
   OV_CK(rot3.ensure(3 * vb));
   OV_CK(t.ensure(vb));
@@ -95,8 +103,9 @@ extern "C" ov_status ov_sign_poly_quad(ov_ctx* c, int order, double lo, double h
   void* rot[3] = {rot3.c(), rot3.c() + vb, rot3.c() + 2 * vb};
   void* b0 = nullptr;
   const void* b2v = nullptr;
-  OV_TRY(clenshaw_forward(c, I, cf, alpha, beta, xchi.p, zero.p, rot, t.p, &b0, &b2v,
-                          [](int, void*) { return OV_OK; }));
+  OV_TRY(clenshaw_forward(
+      c, I, cf, alpha, beta, xchi.p, zero.p, [&](int k) { return rot[k % 3]; }, [&](int) { return t.p; }, &b0, &b2v,
+      [](int, void*) { return OV_OK; }));
   launch_axpby(P, 0.5, b0, -0.5, b2v, gvec.p, V, 1, c->st);  // f_N(Z) chi = (b_0 - b_2)/2
   OV_TRY(launched(c));
   EpiArgs ek;
@@ -110,7 +119,6 @@ extern "C" ov_status ov_sign_poly_quad(ov_ctx* c, int order, double lo, double h
     OV_TRY(unpack_output(c, I, t.p, p_chi, 1, dt));
   }
   OV_CK(cudaStreamSynchronize(c->st));
-  for (DevBuf* b : {&xchi, &rot3, &t, &zero, &gvec, &gbar}) b->release();
   return OV_OK;
 }
 
@@ -127,13 +135,39 @@ extern "C" ov_status ov_sign_poly_grad(ov_ctx* c, int order, double lo, double h
   const double a2 = lo * lo, b2 = hi * hi;
   const double alpha = 2.0 / (b2 - a2), beta = -(b2 + a2) / (b2 - a2);
 
-  // checkpoint slots: k = 16 j + 1 -> 2 j, k = 16 j + 2 -> 2 j + 1
+  // every b_k (k = 0..N) and K b_{k+1} (k = 0..N-1) on the device when they
+  // fit in the allowance; otherwise checkpoint slots k = 16 j + 1 -> 2 j,
+  // k = 16 j + 2 -> 2 j + 1 and segment buffers for the recomputation
+  // (vectors this context already holds for it count as free)
+  GradWork& w = c->gw;
+  size_t allowance;
+  if (c->grad_mem < 0) {
+    size_t fr = 0, tot = 0;
+    OV_CK(cudaMemGetInfo(&fr, &tot));
+    allowance = (fr + w.keep.bytes) / 2;
+  } else {
+    allowance = (size_t)c->grad_mem;
+  }
+  const bool keep_all = vb * (size_t)(2 * N + 1) <= allowance;
   const int nck = 2 * (N / kSeg + 2);
-  DevBuf xchi, ck, segb, segt, bbar, tbar, gvec, gbar, zero, t, G;
+  DevBuf &xchi = w.xchi, &ck = w.ck, &segb = w.segb, &segt = w.segt, &bbar = w.bbar, &tbar = w.tbar;
+  DevBuf &gvec = w.gvec, &gbar = w.gbar, &zero = w.zero, &t = w.t, &G = w.G;
   OV_CK(xchi.ensure(vb));
-  OV_CK(ck.ensure(vb * nck));
-  OV_CK(segb.ensure(vb * (kSeg + 2)));
-  OV_CK(segt.ensure(vb * (kSeg + 1)));
+  if (keep_all) {  // b_k in slots 0..N, K b_{k+1} in slots N+1..2N
+    if (w.keep.bytes < vb * (size_t)(2 * N + 1)) {
+      OV_CK(cudaStreamSynchronize(c->st));
+      w.keep.release();
+    }
+    OV_CK(w.keep.ensure(vb * (size_t)(2 * N + 1)));
+    ck.release();
+    segb.release();
+    segt.release();
+  } else {
+    w.keep.release();
+    OV_CK(ck.ensure(vb * nck));
+    OV_CK(segb.ensure(vb * (kSeg + 2)));
+    OV_CK(segt.ensure(vb * (kSeg + 1)));
+  }
   OV_CK(bbar.ensure(vb * (kSeg + 2)));
   OV_CK(tbar.ensure(vb * kSeg));
   OV_CK(gvec.ensure(vb));
@@ -145,7 +179,10 @@ extern "C" ov_status ov_sign_poly_grad(ov_ctx* c, int order, double lo, double h
   OV_CK(cudaMemsetAsync(zero.p, 0, vb, c->st));
   OV_CK(cudaMemsetAsync(G.p, 0, gbytes, c->st));
   OV_TRY(pack_input(c, I, chi, 1, dt, xchi.p));
+  c->stats.grad_kept_terms = keep_all ? 2 * N + 1 : nck;
   auto slot = [&](DevBuf& b, int i) { return static_cast<void*>(b.c() + (size_t)i * vb); };
+  auto Bk = [&](int k) { return slot(w.keep, k); };          // b_k, k = 0..N
+  auto Tk = [&](int k) { return slot(w.keep, N + 1 + k); };  // K b_{k+1}, k = 0..N-1
   auto ck_slot = [&](int k) -> void* {
     if (k > N) return zero.p;
     if (k % kSeg == 1) return slot(ck, 2 * (k / kSeg));
@@ -170,16 +207,23 @@ extern "C" ov_status ov_sign_poly_grad(ov_ctx* c, int order, double lo, double h
     return k_step(c, I, tk1, out, 1, e);
   };
 
-  // ---- forward sweep: b_k for k = N .. 0, rotating through three vectors
-  void* rot[3] = {slot(segb, 0), slot(segb, 1), slot(segb, 2)};
+  // ---- forward sweep: b_k for k = N .. 0, each in its own slot (keep_all) or
+  // rotating through three vectors with copies to the checkpoints
   void* b0 = nullptr;
   const void* b2v = nullptr;
-  OV_TRY(clenshaw_forward(c, I, cf, alpha, beta, xchi.p, zero.p, rot, t.p, &b0, &b2v,
-                          [&](int k, void* bk) -> ov_status {
-                            if (void* cs = (k >= 1) ? ck_slot(k) : nullptr)
-                              OV_CK(cudaMemcpyAsync(cs, bk, vb, cudaMemcpyDeviceToDevice, c->st));
-                            return OV_OK;
-                          }));
+  if (keep_all) {
+    OV_TRY(clenshaw_forward(
+        c, I, cf, alpha, beta, xchi.p, zero.p, [&](int k) { return Bk(k); },
+        [&](int k) { return k < N ? Tk(k) : t.p; }, &b0, &b2v, [](int, void*) { return OV_OK; }));
+  } else {
+    void* rot[3] = {slot(segb, 0), slot(segb, 1), slot(segb, 2)};
+    OV_TRY(clenshaw_forward(c, I, cf, alpha, beta, xchi.p, zero.p, [&](int k) { return rot[k % 3]; },
+                            [&](int) { return t.p; }, &b0, &b2v, [&](int k, void* bk) -> ov_status {
+                              if (void* cs = (k >= 1) ? ck_slot(k) : nullptr)
+                                OV_CK(cudaMemcpyAsync(cs, bk, vb, cudaMemcpyDeviceToDevice, c->st));
+                              return OV_OK;
+                            }));
+  }
   // g = (b_0 - b_2)/2 ; gbar = K chi
   launch_axpby(P, 0.5, b0, -0.5, b2v, gvec.p, V, 1, c->st);
   OV_TRY(launched(c));
@@ -197,8 +241,11 @@ extern "C" ov_status ov_sign_poly_grad(ov_ctx* c, int order, double lo, double h
       OV_CK(cudaMemcpyAsync(slot(bbar, 0), slot(bbar, kSeg), vb, cudaMemcpyDeviceToDevice, c->st));
       OV_CK(cudaMemcpyAsync(slot(bbar, 1), slot(bbar, kSeg + 1), vb, cudaMemcpyDeviceToDevice, c->st));
     }
-    // recompute b_j and t_j = K b_j for j = k0+1 .. k1+1 (segb/segt slot j - k0 - 1)
-    {
+    // b_{k+1} and K b_{k+1} for the adjoint steps k = k0 .. k1
+    auto b_next = [&](int k) { return keep_all ? Bk(k + 1) : slot(segb, k - k0); };
+    auto t_next = [&](int k) { return keep_all ? Tk(k) : slot(segt, k - k0); };
+    if (!keep_all) {
+      // recompute b_j and t_j = K b_j for j = k0+1 .. k1+1 (segb/segt slot j - k0 - 1)
       const int top = k1 + 1;
       // from b_{k0+17}, b_{k0+18} (checkpoints; zero above N) down to b_{k0+1}
       const void* p1 = ck_slot(k0 + kSeg + 1);
@@ -233,11 +280,11 @@ extern "C" ov_status ov_sign_poly_grad(ov_ctx* c, int order, double lo, double h
       void* tb_k = slot(tbar, k - k0);
       OV_TRY(k_step(c, I, bb_k, tb_k, 1, ek));  // tbar_k = K bbar_k
       pairs.u[pairs.n] = bb_k;
-      pairs.v[pairs.n] = slot(segt, k - k0);  // t_{k+1}
+      pairs.v[pairs.n] = t_next(k);  // K b_{k+1}
       pairs.w[pairs.n] = 2.0 * alpha;
       pairs.n++;
       pairs.u[pairs.n] = tb_k;
-      pairs.v[pairs.n] = slot(segb, k - k0);  // b_{k+1}
+      pairs.v[pairs.n] = b_next(k);  // b_{k+1}
       pairs.w[pairs.n] = 2.0 * alpha;
       pairs.n++;
       if (k + 1 <= N - 1) {  // bbar_{k+1} = 2 alpha K tbar_k + 2 beta bbar_k - bbar_{k-1} [- gbar/2 at k+1 = 2]
@@ -265,6 +312,13 @@ extern "C" ov_status ov_sign_poly_grad(ov_ctx* c, int order, double lo, double h
   launch_force_finish(P, G.p, V, dout, c->st);
   OV_TRY(launched(c));
   OV_TRY(finish_out(c, grad_links, obytes, staged));
-  for (DevBuf* b : {&xchi, &ck, &segb, &segt, &bbar, &tbar, &gvec, &gbar, &zero, &t, &G}) b->release();
+  return OV_OK;
+}
+
+extern "C" ov_status ov_set_grad_memory(ov_ctx* c, long long bytes) {
+  if (!c) return OV_ERR_INVALID;
+  c->grad_mem = bytes < 0 ? -1 : bytes;
+  OV_CK(cudaStreamSynchronize(c->st));
+  c->gw.release();
   return OV_OK;
 }

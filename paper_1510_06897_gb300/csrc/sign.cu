@@ -76,12 +76,13 @@ ov_status sign_core(ov_ctx* c, Inst& I, const void* in, void* out, int nrhs, Kin
   //     d = sum sgn(lambda_i) c_i phi_i  (both scaled by `scale`).  Several
   //     right-hand sides: one Gram launch reads every eigenvector once for all
   //     of them (c stored [i][r]); one right-hand side: the projection kernel.
-  const bool batched = (n_ev > 0 && nrhs > 1 && n_ev <= gram_max_vectors() && nrhs <= gram_max_vectors());
+  //     The tensor-core Gram takes up to 128 eigenvectors, the CUDA-core one 64.
+  const char* mode = std::getenv("OV_DEFL_GEMM");
+  const bool tc = I.pv == OP_F32 && n_ev > 0 && nrhs > 1 && n_ev <= tc_gram_max_rows() &&
+                  nrhs <= tc_gram_max_rhs() && !(mode && std::strcmp(mode, "cuda") == 0);
+  const bool batched = n_ev > 0 && nrhs > 1 && (tc || (n_ev <= gram_max_vectors() && nrhs <= gram_max_vectors()));
   if (batched) {
     OV_CK(c->d_gram.ensure(sizeof(double2) * (size_t)n_ev * nrhs * kReduceBlocks));
-    const char* mode = std::getenv("OV_DEFL_GEMM");
-    const bool tc = I.pv == OP_F32 && n_ev <= tc_gram_max_rows() && nrhs <= tc_gram_max_rhs() &&
-                    !(mode && std::strcmp(mode, "cuda") == 0);
     int nblk = kReduceBlocks;
     if (tc) {
       // tensor cores: one CTA per SM, TF32 x 3 split products

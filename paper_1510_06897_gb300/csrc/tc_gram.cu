@@ -4,21 +4,26 @@
 // layout (each vector a contiguous array of 24 V floats, (re, im) pairs).
 //
 // Real form: with a = phi_i and b = psi_j as interleaved (re, im) arrays,
-//   Re C = sum a . b,   Im C = sum a . b~,   b~ = (b_im, -b_re) per pair,
-// so one real GEMM D[128 x 32] = A[128 x K] B[32 x K]^T with A rows = phi_i
-// (n_ev <= 128, zero rows above) and B rows = (b_j, b~_j) (2 nrhs <= 32)
-// gives both.  Each FP32 operand is split into TF32 parts x = hi + lo and
-// D += A_hi B_hi + A_hi B_lo + A_lo B_hi (tcgen05.mma kind::tf32, FP32
-// accumulators in tensor memory).  K is split over CTAs (one per SM); every
-// kFlush chunks a CTA adds its tensor-memory accumulator into FP64 registers
-// and restarts it, and at the end writes one FP64 partial per (i, j), which
-// the fixed-order reduction of blas.cu sums.
+//   Re C = sum a . b,   Im C = sum a . b~,   b~ = (b_im, -b_re) per pair.
+// Each FP32 operand is split into TF32 parts x = hi + lo.  The B tile (the
+// MMA's N side, 64 rows) holds b_j and b~_j as hi parts in rows 0 .. 2 mb - 1
+// and as lo parts in rows 32 .. 32 + 2 mb - 1.  For n_ev <= 64 the A tile
+// (M = 128) holds a_i hi in row i and a_i lo in row 64 + i, so ONE
+// tcgen05.mma kind::tf32 per 8-wide K step yields all four products
+// hi.hi, hi.lo (columns 0-31, 32-63 of lanes 0-63) and lo.hi, lo.lo (lanes
+// 64-127); the lo.lo term is below the FP32 level but costs nothing.  For
+// 64 < n_ev <= 128 the hi and lo parts of A sit in two 128-row tiles and two
+// MMAs per K step accumulate into the same lanes.  FP32 accumulators live in
+// tensor memory.  K is split over CTAs (one per SM); every kFlush chunks a
+// CTA adds its tensor-memory accumulator into FP64 registers and restarts
+// it, and at the end writes one FP64 partial per (i, j), which the
+// fixed-order reduction of blas.cu sums.
 //
 // Pipeline per CTA (512 threads): raw 64-float chunks of every row are copied
 // into a ring of up to four shared-memory buffers with cp.async (several
 // chunks in flight), then split and stored into one of two MMA stages in the
 // canonical no-swizzle K-major layout (8-row x 16-byte core matrices); one
-// thread issues the 24 MMAs of the chunk and commits them to the stage's
+// thread issues the chunk's 8 (or 16) MMAs and commits them to the stage's
 // mbarrier, so the next chunk is loaded while the tensor core works.  Every
 // mbarrier wait is bounded (about a second); on expiry the kernel records an
 // error flag, waits (bounded) for its own MMAs, frees its tensor memory and
@@ -30,22 +35,24 @@ namespace ov {
 
 namespace {
 
-constexpr int kTcM = 128;      // MMA M: rows of A (eigenvectors, zero padded)
-constexpr int kTcN = 32;       // MMA N: 2 x right-hand sides (zero padded)
+constexpr int kTcM = 128;      // MMA M: A tile rows
+constexpr int kTcN = 64;       // MMA N: B tile rows (hi parts in 0..31, lo parts in 32..63)
+constexpr int kLoRow = 32;     // first B row of the lo parts
+constexpr int kPackRows = 64;  // n_ev <= 64: a_i lo in A row 64 + i
 constexpr int kTcK = 64;       // floats per chunk and stage
 constexpr int kTcThreads = 512;
 constexpr int kRawPitch = kTcK * 4 + 16;  // bytes per raw row (padded: conflict-free 16-byte reads)
 constexpr int kRawStagesMax = 4;          // chunks in flight (cp.async ring of raw FP32 rows)
 constexpr int kFlush = 64;     // chunks per tensor-memory accumulation window
-constexpr int kTmemCols = 32;
+constexpr int kTmemCols = 64;
 
-constexpr uint32_t kTileA = kTcM * kTcK * 4;  // bytes of one A part (hi or lo)
+constexpr uint32_t kTileA = kTcM * kTcK * 4;  // bytes of one A tile
 constexpr uint32_t kTileB = kTcN * kTcK * 4;
-constexpr uint32_t kStage = 2 * kTileA + 2 * kTileB;  // A_hi, A_lo, B_hi, B_lo
-constexpr uint32_t kCtrl = 1024;                         // mbarriers, tensor-memory address
+constexpr uint32_t kCtrl = 1024;                     // mbarriers, tensor-memory address
+__host__ __device__ inline uint32_t stage_bytes(int ma) { return (ma <= kPackRows ? 1u : 2u) * kTileA + kTileB; }
 // dynamic shared memory: two MMA stages, control block, raw ring
-inline uint32_t raw_stages(int rows) {
-  const uint32_t avail = 227u * 1024u - 2 * kStage - kCtrl;
+inline uint32_t raw_stages(int ma, int rows) {
+  const uint32_t avail = 227u * 1024u - 2 * stage_bytes(ma) - kCtrl;
   const uint32_t per = (uint32_t)rows * kRawPitch;
   const uint32_t n = avail / per;
   return n < 1 ? 1 : (n > (uint32_t)kRawStagesMax ? (uint32_t)kRawStagesMax : n);
@@ -65,7 +72,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
          (1ull << 46);
 }
 
-// Instruction descriptor, kind::tf32: D FP32, A and B TF32, both K-major, N = 32, M = 128.
+// Instruction descriptor, kind::tf32: D FP32, A and B TF32, both K-major, N = 64, M = 128.
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
                             ((uint32_t)(kTcM >> 4) << 24);
 
@@ -155,6 +162,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               double2* __restrict__ partial, int* __restrict__ err, int nraw, const int* stall,
               long long stall_cycles) {
   extern __shared__ __align__(1024) unsigned char smem[];
+  const bool packed = ma <= kPackRows;
+  const uint32_t kStage = stage_bytes(ma);
+  const uint32_t offB = kStage - kTileB;  // B tile after the one or two A tiles
   unsigned char* stage_base = smem;
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + 2 * kStage);  // [0], [1]: stages
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + 2 * kStage + 64);
@@ -164,7 +174,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int tid = threadIdx.x, warp = tid >> 5;
   const long long half_k = K / 2;  // gamma5 flips the second half of each vector (spins 2, 3)
 
-  // zero both MMA stages once: rows >= ma / >= 2 mb stay zero
+  // zero both MMA stages once: rows no chunk writes stay zero
   for (uint32_t i = tid; i < 2 * kStage / 16; i += kTcThreads)
     reinterpret_cast<uint4*>(stage_base)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
@@ -199,6 +209,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     cp_async_commit();
   };
 
+  // FP64 sums of the hi-column (0..31) and lo-column (32..63) accumulators of this thread's lane
   double acc[32];
 #pragma unroll
   for (int i = 0; i < 32; ++i) acc[i] = 0.0;
@@ -217,7 +228,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_after();
     if (!failed && warp < 4 && in_window > 0) {
       float v[32];
-      tc_load32(tmem + ((uint32_t)(warp * 32) << 16), v);
+      const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+      tc_load32(lane_base, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) acc[i] += (double)v[i];
+      tc_load32(lane_base + kLoRow, v);
 #pragma unroll
       for (int i = 0; i < 32; ++i) acc[i] += (double)v[i];
     }
@@ -247,7 +262,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       failed = true;
       break;
     }
-    // split raw rows into TF32 hi / lo tiles; consecutive threads take
+    // split raw rows into TF32 hi / lo parts; consecutive threads take
     // consecutive rows (conflict-free 16-byte reads and writes)
     const unsigned char* raw = raw_base + (uint32_t)slot * raw_stage_bytes;
     const long long k0 = ch * kTcK;
@@ -260,9 +275,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         split_tf32(x.y, hi.y, lo.y);
         split_tf32(x.z, hi.z, lo.z);
         split_tf32(x.w, hi.w, lo.w);
-        const uint32_t off = tile_off(row, 4 * q);
-        *reinterpret_cast<float4*>(st + off) = hi;
-        *reinterpret_cast<float4*>(st + kTileA + off) = lo;
+        *reinterpret_cast<float4*>(st + tile_off(row, 4 * q)) = hi;
+        if (packed) *reinterpret_cast<float4*>(st + tile_off(kPackRows + row, 4 * q)) = lo;
+        else *reinterpret_cast<float4*>(st + kTileA + tile_off(row, 4 * q)) = lo;
       } else {
         const int j = row - ma;
         if (g5b && k0 + 4 * q >= half_k) x = make_float4(-x.x, -x.y, -x.z, -x.w);
@@ -276,11 +291,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         split_tf32(xt.y, thi.y, tlo.y);
         split_tf32(xt.z, thi.z, tlo.z);
         split_tf32(xt.w, thi.w, tlo.w);
-        const uint32_t off = tile_off(j, 4 * q), offt = tile_off(mb + j, 4 * q);
-        *reinterpret_cast<float4*>(st + 2 * kTileA + off) = hi;
-        *reinterpret_cast<float4*>(st + 2 * kTileA + kTileB + off) = lo;
-        *reinterpret_cast<float4*>(st + 2 * kTileA + offt) = thi;
-        *reinterpret_cast<float4*>(st + 2 * kTileA + kTileB + offt) = tlo;
+        unsigned char* bt = st + offB;
+        *reinterpret_cast<float4*>(bt + tile_off(j, 4 * q)) = hi;
+        *reinterpret_cast<float4*>(bt + tile_off(mb + j, 4 * q)) = thi;
+        *reinterpret_cast<float4*>(bt + tile_off(kLoRow + j, 4 * q)) = lo;
+        *reinterpret_cast<float4*>(bt + tile_off(kLoRow + mb + j, 4 * q)) = tlo;
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -289,18 +304,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_after();
     if (tid == 0) {
       // the descriptor's address field is addr >> 4 in its low bits (all of
-      // this CTA's shared memory stays below 2^18 bytes), so sub-tiles and
-      // K steps are plain offsets of one base descriptor
-      const uint64_t d_ahi = smem_desc(smem_u32(st));
-      const uint64_t d_alo = d_ahi + (kTileA >> 4), d_bhi = d_ahi + ((2 * kTileA) >> 4);
-      const uint64_t d_blo = d_bhi + (kTileB >> 4);
+      // this CTA's shared memory stays below 2^18 bytes), so tiles and K
+      // steps are plain offsets of one base descriptor
+      const uint64_t d_a0 = smem_desc(smem_u32(st));
+      const uint64_t d_a1 = d_a0 + (kTileA >> 4), d_b = d_a0 + (offB >> 4);
 #pragma unroll
       for (int kk = 0; kk < kTcK / 8; ++kk) {
         const uint64_t o = (uint64_t)kk * (256 >> 4);  // 8 floats = two core matrices along K
         const uint32_t acc_in = (in_window > 0 || kk > 0) ? 1u : 0u;
-        tc_mma(tmem, d_ahi + o, d_bhi + o, acc_in);
-        tc_mma(tmem, d_ahi + o, d_blo + o, 1u);
-        tc_mma(tmem, d_alo + o, d_bhi + o, 1u);
+        tc_mma(tmem, d_a0 + o, d_b + o, acc_in);
+        if (!packed) tc_mma(tmem, d_a1 + o, d_b + o, 1u);
       }
       tc_commit(smem_u32(&bars[stage]));
     }
@@ -317,11 +330,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // bounded wait (no stall) for this CTA's own MMAs before releasing tensor memory
     if (last_stage >= 0) mbar_wait(smem_u32(&bars[last_stage]), last_parity);
   }
+  if (!failed && packed) {
+    // lanes 64 + i hold the lo.hi and lo.lo products of row i: add them into lane i
+    // (the stages are free: the last flush waited for every MMA)
+    double* fold = reinterpret_cast<double*>(stage_base);
+    if (tid >= kPackRows && tid < 2 * kPackRows) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) fold[(tid - kPackRows) * 33 + i] = acc[i];
+    }
+    __syncthreads();
+    if (tid < kPackRows) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) acc[i] += fold[tid * 33 + i];
+    }
+  }
   if (!failed && warp < 4) {
     const int row = tid;  // warps 0-3: lane quarter = rows 0..127
-    if (row < ma) {
-      for (int j = 0; j < mb; ++j)
-        partial[((long long)row * mb + j) * gridDim.x + blockIdx.x] = make_double2(acc[j], acc[mb + j]);
+    if (row < ma) {  // acc[j] = Re, acc[mb + j] = Im of C_row,j (static indices keep acc in registers)
+      double* pd = reinterpret_cast<double*>(partial);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        if (c < mb) pd[2 * (((long long)row * mb + c) * gridDim.x + blockIdx.x)] = acc[c];
+        else if (c < 2 * mb) pd[2 * (((long long)row * mb + c - mb) * gridDim.x + blockIdx.x) + 1] = acc[c];
+      }
     }
   }
   tc_fence_before();
@@ -334,13 +365,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }  // namespace
 
 int tc_gram_max_rows() { return kTcM; }
-int tc_gram_max_rhs() { return kTcN / 2; }
+int tc_gram_max_rhs() { return kLoRow / 2; }
 
 cudaError_t launch_tc_gram(const void* A, int ma, const void* B, int mb, int64_t V, int g5b, double2* partial,
                            int nblk, int* err, const int* stall, long long stall_cycles, cudaStream_t st) {
-  if (ma < 1 || ma > kTcM || mb < 1 || 2 * mb > kTcN) return cudaErrorInvalidValue;
-  const uint32_t nraw = raw_stages(ma + mb);
-  const uint32_t smem = 2 * kStage + kCtrl + nraw * (uint32_t)(ma + mb) * kRawPitch;
+  if (ma < 1 || ma > kTcM || mb < 1 || 2 * mb > kLoRow) return cudaErrorInvalidValue;
+  const uint32_t nraw = raw_stages(ma, ma + mb);
+  const uint32_t smem = 2 * stage_bytes(ma) + kCtrl + nraw * (uint32_t)(ma + mb) * kRawPitch;
   cudaError_t e = cudaFuncSetAttribute(k_tc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_tc_gram<<<nblk, kTcThreads, smem, st>>>(static_cast<const float*>(A), ma, static_cast<const float*>(B), mb,

@@ -78,6 +78,7 @@ def test_null_context_calls(lib):
     assert lib.ov_solve_gmresr(None, 0.1, 1e-10, 10, None, None, 1, 0, None, None) == binding.OV_ERR_INVALID
     assert lib.ov_set_gmresr_params(None, 0, 0.1, 100, 8) == binding.OV_ERR_INVALID
     assert lib.ov_enable_fp32_operator(None, None) == binding.OV_ERR_INVALID
+    assert lib.ov_set_grad_memory(None, 0) == binding.OV_ERR_INVALID
 
 
 def test_stout_smear_rejects_bad_arguments_before_device_work(lib):

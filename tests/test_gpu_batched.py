@@ -223,11 +223,14 @@ def test_batched_solve_three_rhs():
         assert np.linalg.norm(true_r) / np.linalg.norm(rhs) <= 2 * tol
 
 
-@pytest.mark.parametrize("dims,n_ev,nrhs", [((8, 8, 8, 8), 40, 12), ((3, 3, 3, 5), 20, 7)])
+@pytest.mark.parametrize("dims,n_ev,nrhs", [((8, 8, 8, 8), 40, 12), ((3, 3, 3, 5), 20, 7), ((4, 4, 4, 8), 64, 16),
+                                            ((4, 4, 4, 8), 65, 3), ((6, 6, 6, 6), 128, 16)])
 def test_tensor_core_projection(monkeypatch, dims, n_ev, nrhs):
-    """The tcgen05 projection (TF32 x 3) against the CUDA-core FP64-sum Gram
-    kernel on the same inputs, through sign(K) and D^dagger (gamma5 on the
-    input), including a K tail that is not a multiple of the 64-float chunk."""
+    """The tcgen05 projection (TF32 split products) against the CUDA-core
+    FP64-sum Gram kernel on the same inputs, through sign(K) and D^dagger
+    (gamma5 on the input), including a K tail that is not a multiple of the
+    64-float chunk; n_ev <= 64 packs the hi and lo parts of the eigenvectors
+    into one tile, 65..128 uses two tiles; 16 right-hand sides fill the B tile."""
     links = inputs.gauge_links(dims, seed=8301)
     src = inputs.gaussian_source(dims, seed=8302, nrhs=nrhs)
     evecs = _random_orthonormal(dims, n_ev, 8303)
