@@ -117,30 +117,14 @@ __global__ void __launch_bounds__(128) k_force_pairs(Lattice g, const void* __re
 template <int N>
 __device__ __forceinline__ void cp_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// cp.async of pair p's u and v over the box and faces into stage p % NS:
-// 16-byte chunks, consecutive threads on consecutive slots of one chunk
-template <class T, class TG, class R>
-__device__ __forceinline__ void force_tile_issue(const Lattice& g, unsigned char* sm, const int* ext,
-                                                 const PairArgsDev<R>& P, int p) {
-  const uint32_t base = (uint32_t)__cvta_generic_to_shared(sm + (p % TG::NS) * TG::STAGE);
-  for (int idx = threadIdx.x; idx < 2 * TG::CH * TG::NE; idx += 4 * TG::NB) {
-    const int e = idx % TG::NE, r = idx / TG::NE;  // r = which * CH + chunk
-    const int which = r / TG::CH, ch = r % TG::CH;
-    const char* src = (which ? P.v[p] : P.u[p]) + ((int64_t)ch * g.V + ext[e]) * 16;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(base + (uint32_t)(r * TG::NE + e) * 16u),
-                 "l"(src)
-                 : "memory");
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
 // Shared-memory tiled form of the same sums.  A block covers a
 // BX x BY x BZ x BT box of sites and thread (mu, i) the link (box site i, mu).
 // For every pair, u and v over the box and its +x, +y, +z, +t faces are
 // copied into shared memory once with cp.async, three stages deep (pairs
 // p + 1 and p + 2 land while pair p is used; one barrier per pair), so each
 // vector leaves L2 about
-// (box + faces) / box times (2.25 for 4 x 4 x 4 x 2) instead of once for the
+// (box + faces) / box times (2.4 for 8 x 4 x 2 x 2: rows of 8 sites are whole
+// 128-byte lines of each FP32 chunk array) instead of once for the
 // site and once more for every direction that reaches it from outside the
 // block.  The pairs are folded in the same order with the same arithmetic as
 // k_force_pairs.
@@ -153,6 +137,8 @@ struct ForceTile {
   static constexpr int STAGE = 2 * CH * NE * 16;                 // u and v of one pair
   static constexpr int NS = 3;                                   // stages
   static constexpr int SMEM = NS * STAGE + NE * 4;               // stages + site table
+  static constexpr int NT = 4 * NB;                              // threads
+  static constexpr int NI = (2 * CH * NE + NT - 1) / NT;         // copy items per thread and pair
   static bool fits(const LatticeH& g) {
     return g.L[0] % BX == 0 && g.L[1] % BY == 0 && g.L[2] % BZ == 0 && g.L[3] % BT == 0;
   }
@@ -242,7 +228,7 @@ __global__ void __launch_bounds__(4 * BX * BY * BZ * BT, 1)
   const int Z0 = (b % nbz) * BZ;
   const int T0 = (b / nbz) * BT;
   // lattice site of every slot: box sites, then the +x, +y, +z, +t faces
-  for (int e = tid; e < TG::NE; e += 4 * TG::NB) {
+  for (int e = tid; e < TG::NE; e += TG::NT) {
     int c[4];
     if (e < TG::NB) {
       c[0] = e % BX;
@@ -279,6 +265,33 @@ __global__ void __launch_bounds__(4 * BX * BY * BZ * BT, 1)
     ext[e] = gx + g.L[0] * (gy + g.L[1] * (gz + g.L[2] * gt));
   }
   __syncthreads();
+  // Copy items of this thread, the same for every pair: item idx = tid + m NT
+  // is 16-byte chunk (idx / NE) % CH of slot idx % NE of u (idx < CH NE) or
+  // v, which lands at byte 16 idx of the stage; its source is chunk-array
+  // element ch V + site (< 12 * 2^27, 32 bits).
+  uint32_t item[TG::NI];
+#pragma unroll
+  for (int m = 0; m < TG::NI; ++m) {
+    const int idx = tid + m * TG::NT;
+    item[m] = idx < 2 * TG::CH * TG::NE
+                  ? (uint32_t)(((idx / TG::NE) % TG::CH) * g.V) + (uint32_t)ext[idx % TG::NE]
+                  : 0u;
+  }
+  auto issue = [&](int p) {  // pair p's u and v into stage p % NS
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(fsm + (p % TG::NS) * TG::STAGE);
+    const char* u = P.u[p];
+    const char* v = P.v[p];
+#pragma unroll
+    for (int m = 0; m < TG::NI; ++m) {
+      const int idx = tid + m * TG::NT;
+      if (idx < 2 * TG::CH * TG::NE) {
+        const char* src = (idx < TG::CH * TG::NE ? u : v) + (uint64_t)item[m] * 16u;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(base + (uint32_t)idx * 16u), "l"(src)
+                     : "memory");
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
   const int mu = tid / TG::NB, i = tid % TG::NB;  // mu is warp-uniform: NB is a multiple of 32
   const int ix = i % BX, iy = (i / BX) % BY, iz = (i / (BX * BY)) % BZ, it = i / (BX * BY * BZ);
   int nb;  // slot of site i + mu
@@ -290,14 +303,14 @@ __global__ void __launch_bounds__(4 * BX * BY * BZ * BT, 1)
 #pragma unroll
   for (int k = 0; k < 9; ++k) A[k] = B[k] = {R(0), R(0)};
   static_assert(TG::NS == 3, "the waits below assume three stages");
-  if (P.n > 0) force_tile_issue<T, TG>(g, fsm, ext, P, 0);
-  if (P.n > 1) force_tile_issue<T, TG>(g, fsm, ext, P, 1);
+  if (P.n > 0) issue(0);
+  if (P.n > 1) issue(1);
   for (int p = 0; p < P.n; ++p) {
     // groups committed so far: pairs 0 .. min(p + 1, n - 1); pair p must be complete
     if (p + 1 < P.n) cp_wait_group<1>();
     else cp_wait_group<0>();
     __syncthreads();  // every thread's copies of pair p have landed; pair p - 1 is used up
-    if (p + 2 < P.n) force_tile_issue<T, TG>(g, fsm, ext, P, p + 2);  // into the stage of pair p - 1
+    if (p + 2 < P.n) issue(p + 2);  // into the stage of pair p - 1
     const unsigned char* st = fsm + (p % TG::NS) * TG::STAGE;
     const R w = P.w[p];
     switch (mu) {
@@ -353,7 +366,7 @@ void launch_force_pairs(OpPrec p, const LatticeH& gh, const void* links, const F
   } else {
     PairArgsDev<float> P;
     args(&P);
-    if (ForceTile<F32, 4, 4, 4, 2>::fits(gh)) launch_force_tile<F32, 4, 4, 4, 2>(g, links, P, G, st);
+    if (ForceTile<F32, 8, 4, 2, 2>::fits(gh)) launch_force_tile<F32, 8, 4, 2, 2>(g, links, P, G, st);
     else k_force_pairs<F32><<<grid, 128, 0, st>>>(g, links, P, G);
   }
 }

@@ -19,15 +19,22 @@
 // it, and at the end writes one FP64 partial per (i, j), which the
 // fixed-order reduction of blas.cu sums.
 //
-// Pipeline per CTA (512 threads): raw 64-float chunks of every row are copied
-// into a ring of up to four shared-memory buffers with cp.async (several
-// chunks in flight), then split and stored into one of two MMA stages in the
-// canonical no-swizzle K-major layout (8-row x 16-byte core matrices); one
-// thread issues the chunk's 8 (or 16) MMAs and commits them to the stage's
-// mbarrier, so the next chunk is loaded while the tensor core works.  Every
-// mbarrier wait is bounded (about a second); on expiry the kernel records an
-// error flag, waits (bounded) for its own MMAs, frees its tensor memory and
-// returns.
+// Pipeline per CTA (512 threads, warp-specialised): 15 worker warps copy raw
+// 64-float chunks of every row into a ring of up to six shared-memory
+// buffers with cp.async (several chunks in flight), each lane owning the
+// same 16-byte pieces of every chunk, so it reads back only its own copies
+// and no CTA barrier guards the ring; they split the pieces into TF32 hi / lo
+// parts in one of two or three MMA stages (canonical no-swizzle K-major
+// layout, 8-row x 16-byte core matrices) and arrive on the stage's "filled"
+// mbarrier.  Lane 0 of the last warp waits on it, issues the chunk's 8 (or
+// 16) MMAs and commits them to the stage's "consumed" mbarrier, which the
+// workers wait on before refilling the stage.  The CTA synchronises only when
+// it moves the tensor-memory accumulator into FP64 registers (every 64
+// chunks).  Every mbarrier wait is bounded (about a second); on expiry a
+// thread raises a shared abort flag, every thread runs the rest of its
+// iterations without work (so the flush barriers still match), the kernel
+// records an error flag, waits (bounded) for its own copies and MMAs in
+// flight, frees its tensor memory and returns.
 #include "common.cuh"
 #include "internal.h"
 
@@ -40,9 +47,11 @@ constexpr int kTcN = 64;       // MMA N: B tile rows (hi parts in 0..31, lo part
 constexpr int kLoRow = 32;     // first B row of the lo parts
 constexpr int kPackRows = 64;  // n_ev <= 64: a_i lo in A row 64 + i
 constexpr int kTcK = 64;       // floats per chunk and stage
-constexpr int kTcThreads = 512;
+constexpr int kWorkerWarps = 15;         // copy and split
+constexpr int kWorkers = 32 * kWorkerWarps;
+constexpr int kTcThreads = kWorkers + 32;  // + one warp whose lane 0 issues the MMAs
 constexpr int kRawPitch = kTcK * 4 + 16;  // bytes per raw row (padded: conflict-free 16-byte reads)
-constexpr int kRawStagesMax = 4;          // chunks in flight (cp.async ring of raw FP32 rows)
+constexpr int kRawStagesMax = 6;          // chunks in flight (cp.async ring of raw FP32 rows)
 constexpr int kFlush = 64;     // chunks per tensor-memory accumulation window
 constexpr int kTmemCols = 64;
 
@@ -50,12 +59,19 @@ constexpr uint32_t kTileA = kTcM * kTcK * 4;  // bytes of one A tile
 constexpr uint32_t kTileB = kTcN * kTcK * 4;
 constexpr uint32_t kCtrl = 1024;                     // mbarriers, tensor-memory address
 __host__ __device__ inline uint32_t stage_bytes(int ma) { return (ma <= kPackRows ? 1u : 2u) * kTileA + kTileB; }
-// dynamic shared memory: two MMA stages, control block, raw ring
-inline uint32_t raw_stages(int ma, int rows) {
-  const uint32_t avail = 227u * 1024u - 2 * stage_bytes(ma) - kCtrl;
+// dynamic shared memory: nstage MMA stages, control block, raw ring of
+// nraw chunks.  Three MMA stages when they leave room for a ring of at least
+// four chunks (the hi / lo-packed tile), else two.
+constexpr uint32_t kSmemMax = 227u * 1024u;
+inline uint32_t raw_stages(int ma, int rows, int nstage) {
+  const uint32_t avail = kSmemMax - (uint32_t)nstage * stage_bytes(ma) - kCtrl;
   const uint32_t per = (uint32_t)rows * kRawPitch;
   const uint32_t n = avail / per;
   return n < 1 ? 1 : (n > (uint32_t)kRawStagesMax ? (uint32_t)kRawStagesMax : n);
+}
+inline int mma_stages(int ma, int rows) {
+  const uint64_t need3 = 3ull * stage_bytes(ma) + kCtrl + 4ull * (uint64_t)rows * kRawPitch;
+  return need3 <= kSmemMax ? 3 : 2;
 }
 
 // byte offset of element (row r, k) inside one part: core matrices of
@@ -84,22 +100,26 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
 }
 
+// One try_wait with a suspend-time hint: a thread whose phase is not yet
+// complete is parked (up to ~0.1 ms) instead of spinning, so the warps that
+// wait do not take issue slots from the ones that work.
 __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(100000u)
       : "memory");
   return ok != 0;
 }
 
-// Bounded wait: false if the phase did not complete within ~2^31 cycles.
-// stall (testing, see ov_test_wait_expiry): a device flag that nothing sets;
-// when given, the wait first waits up to stall_cycles for it, runs out and
-// reports failure as an expired wait would.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* stall = nullptr,
-                                          long long stall_cycles = 0) {
+// Bounded wait: false if the phase did not complete within ~2^31 cycles or
+// another thread of the CTA raised *abort.  stall (testing, see
+// ov_test_wait_expiry): a device flag that nothing sets; when given, the wait
+// first waits up to stall_cycles for it, runs out and reports failure as an
+// expired wait would.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort,
+                                          const volatile int* stall = nullptr, long long stall_cycles = 0) {
   const long long t0 = clock64();
   if (stall != nullptr) {
     while (*stall == 0) {
@@ -107,9 +127,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const v
     }
   }
   while (!mbar_test(bar, parity)) {
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if ((abort != nullptr && *abort != 0) || clock64() - t0 > (1ll << 31)) return false;
   }
   return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -157,29 +181,40 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// 16 warps of <= 128 registers: each scheduler's quarter of the register file holds its four warps
+template <int NI>  // 16-byte pieces per worker thread and chunk
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gram(const float* __restrict__ A, int ma, const float* __restrict__ B, int mb, long long K, int g5b,
-              double2* __restrict__ partial, int* __restrict__ err, int nraw, const int* stall,
+              double2* __restrict__ partial, int* __restrict__ err, int nstage, int nraw, const int* stall,
               long long stall_cycles) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const bool packed = ma <= kPackRows;
   const uint32_t kStage = stage_bytes(ma);
   const uint32_t offB = kStage - kTileB;  // B tile after the one or two A tiles
   unsigned char* stage_base = smem;
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + 2 * kStage);  // [0], [1]: stages
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + 2 * kStage + 64);
-  unsigned char* raw_base = smem + 2 * kStage + kCtrl;
+  // bars[s]: the MMAs reading stage s completed (tcgen05.commit); bars[4 + s]:
+  // stage s filled (one arrival per worker warp); s < nstage <= 3
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + nstage * kStage);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + nstage * kStage + 64);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + nstage * kStage + 128);
+  unsigned char* raw_base = smem + nstage * kStage + kCtrl;
   const int rows = ma + mb;
+  const int nitem = ((rows + 7) / 8) * 128;  // item space: 8-row groups x 16 pieces
   const uint32_t raw_stage_bytes = (uint32_t)rows * kRawPitch;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool worker = warp < kWorkerWarps;
+  const bool issuer = warp == kWorkerWarps && lane == 0;
   const long long half_k = K / 2;  // gamma5 flips the second half of each vector (spins 2, 3)
 
-  // zero both MMA stages once: rows no chunk writes stay zero
-  for (uint32_t i = tid; i < 2 * kStage / 16; i += kTcThreads)
+  // zero the MMA stages once: rows no chunk writes stay zero
+  for (uint32_t i = tid; i < (uint32_t)nstage * kStage / 16; i += kTcThreads)
     reinterpret_cast<uint4*>(stage_base)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
-    mbar_init(smem_u32(&bars[0]), 1);
-    mbar_init(smem_u32(&bars[1]), 1);
+    for (int b = 0; b < nstage; ++b) {
+      mbar_init(smem_u32(&bars[b]), 1);
+      mbar_init(smem_u32(&bars[4 + b]), kWorkerWarps);
+    }
+    *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -193,94 +228,97 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
 
-  const long long nchunks = (K + kTcK - 1) / kTcK;
-  // raw copy of chunk `chk` into ring slot `slot`: 16 bytes per thread-iteration,
-  // zero-filled past K and for chunks past the end
-  auto issue = [&](long long chk, int slot) {
-    const uint32_t dst0 = smem_u32(raw_base + (uint32_t)slot * raw_stage_bytes);
-    const long long k0 = chk * kTcK;
-    for (int idx = tid; idx < rows * (kTcK / 4); idx += kTcThreads) {
-      const int row = idx / (kTcK / 4), q = idx % (kTcK / 4);
-      const long long k = k0 + 4 * q;
-      const bool ok = chk < nchunks && k < K;
-      const float* src = (row < ma) ? A + (long long)row * K : B + (long long)(row - ma) * K;
-      cp_async16(dst0 + (uint32_t)row * kRawPitch + 16u * q, ok ? src + k : A, ok ? 16u : 0u);
+  const long long nchunks = (K + kTcK - 1) / kTcK;  // K <= 24 * 2^27: nchunks < 2^26
+  // chunks of this CTA: blockIdx.x + it * gridDim.x for it < niter (the same for every thread)
+  const int niter = blockIdx.x < nchunks ? (int)((nchunks - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  bool failed = false;
+  const long long kstep = (long long)gridDim.x * kTcK;  // k0 advance per iteration
+
+  // A worker's pieces are fixed, one set for copying and one for splitting,
+  // each worked out once (everything but the chunk offset k0 is fixed):
+  //  - copy item c = tid + kWorkers m is piece c % 16 of row c / 16: sixteen
+  //    lanes cover one row's 256 contiguous bytes, so each warp copies whole
+  //    lines of two rows (fewer, fuller memory requests);
+  //  - split item i = tid + kWorkers m is piece (i % 128) / 8 of row
+  //    (i / 128) * 8 + i % 8: eight consecutive lanes take eight consecutive
+  //    rows of one piece (conflict-free tile stores).
+  // The two differ, so a named barrier of the worker warps separates the
+  // copies of a chunk from its split.
+  const char* csrc[NI];
+  uint32_t craw[NI];
+  long long clim[NI];
+  bool cval[NI];
+  uint32_t iraw[NI], io0[NI], io1[NI], io2[NI], io3[NI];
+  long long iglim[NI];
+  int ikind[NI];  // 0: none, 1: eigenvector row (A), 2: right-hand-side row (B)
+#pragma unroll
+  for (int m = 0; m < NI; ++m) {
+    const int c = tid + kWorkers * m;
+    const int crow = c >> 4, cq = c & 15;
+    cval[m] = worker && crow < rows;
+    csrc[m] = reinterpret_cast<const char*>(crow < ma ? A + (long long)crow * K : B + (long long)(crow - ma) * K) +
+              16 * cq;
+    craw[m] = (uint32_t)crow * kRawPitch + 16u * cq;
+    clim[m] = K - 4 * cq;  // piece cq of the chunk at k0 lies inside K when k0 < K - 4 cq
+    const int i = tid + kWorkers * m;
+    const int row = (i >> 7) * 8 + (i & 7), q = (i & 127) >> 3;
+    ikind[m] = (!worker || i >= nitem || row >= rows) ? 0 : (row < ma ? 1 : 2);
+    const int jb = row - ma;
+    iraw[m] = (uint32_t)row * kRawPitch + 16u * q;
+    iglim[m] = half_k - 4 * q;  // piece q lies in the gamma5-flipped half when k0 >= half_k - 4 q
+    if (ikind[m] == 1) {
+      io0[m] = tile_off(row, 4 * q);
+      io1[m] = packed ? tile_off(kPackRows + row, 4 * q) : kTileA + tile_off(row, 4 * q);
+      io2[m] = io3[m] = 0;
+    } else {
+      io0[m] = offB + tile_off(jb, 4 * q);
+      io1[m] = offB + tile_off(mb + jb, 4 * q);
+      io2[m] = offB + tile_off(kLoRow + jb, 4 * q);
+      io3[m] = offB + tile_off(kLoRow + mb + jb, 4 * q);
+    }
+  }
+
+  // (ring slots and k0 are passed in: they advance by counters, never by a division)
+  auto issue = [&](bool valid, long long k0, int slot) {  // chunk at k0 into raw slot `slot`
+    if (!failed && valid) {
+      const uint32_t dst0 = smem_u32(raw_base + (uint32_t)slot * raw_stage_bytes);
+#pragma unroll
+      for (int m = 0; m < NI; ++m) {
+        if (!cval[m]) continue;
+        const bool ok = k0 < clim[m];  // zero-filled past K
+        cp_async16(dst0 + craw[m], ok ? csrc[m] + 4 * k0 : reinterpret_cast<const char*>(A), ok ? 16u : 0u);
+      }
     }
     cp_async_commit();
   };
-
-  // FP64 sums of the hi-column (0..31) and lo-column (32..63) accumulators of this thread's lane
-  double acc[32];
-#pragma unroll
-  for (int i = 0; i < 32; ++i) acc[i] = 0.0;
-  int it = 0;           // chunks processed by this CTA
-  int in_window = 0;    // chunks in the current accumulation window
-  bool failed = false;
-  int last_stage = -1;
-  uint32_t last_parity = 0;
-
-  auto flush = [&]() {
-    // all MMAs issued so far are complete once the last commit's phase is
-    if (last_stage >= 0) {
-      const bool ok = mbar_wait(smem_u32(&bars[last_stage]), last_parity, stall, stall_cycles);
-      if (__syncthreads_or(!ok)) failed = true;
+  // this thread's copies of chunk it have landed (groups committed: chunks up to it + nraw - 2)
+  auto raw_wait = [&]() {
+    switch (nraw) {
+      case 6: cp_async_wait<4>(); break;
+      case 5: cp_async_wait<3>(); break;
+      case 4: cp_async_wait<2>(); break;
+      case 3: cp_async_wait<1>(); break;
+      default: cp_async_wait<0>(); break;
     }
-    tc_fence_after();
-    if (!failed && warp < 4 && in_window > 0) {
-      float v[32];
-      const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-      tc_load32(lane_base, v);
-#pragma unroll
-      for (int i = 0; i < 32; ++i) acc[i] += (double)v[i];
-      tc_load32(lane_base + kLoRow, v);
-#pragma unroll
-      for (int i = 0; i < 32; ++i) acc[i] += (double)v[i];
-    }
-    in_window = 0;
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
   };
-
-  // prologue: nraw - 1 chunks in flight
-  for (int p = 0; p < nraw - 1; ++p) issue(blockIdx.x + (long long)p * gridDim.x, p);
-
-  for (long long ch = blockIdx.x; ch < nchunks && !failed; ch += gridDim.x) {
-    const int stage = it & 1;
-    const uint32_t use = (uint32_t)(it >> 1);
-    unsigned char* st = stage_base + stage * kStage;
-    const int slot = it % nraw;
-    issue(ch + (long long)(nraw - 1) * gridDim.x, (it + nraw - 1) % nraw);
-    // this thread's copies of chunk ch have landed (newer groups may still fly)
-    if (nraw == 4) cp_async_wait<3>();
-    else if (nraw == 3) cp_async_wait<2>();
-    else if (nraw == 2) cp_async_wait<1>();
-    else cp_async_wait<0>();
-    bool ok = true;
-    if (use >= 1) ok = mbar_wait(smem_u32(&bars[stage]), (use - 1) & 1, stall, stall_cycles);  // stage free again
-    if (__syncthreads_or(!ok)) {  // also makes every thread's raw copies visible
-      failed = true;
-      break;
-    }
-    // split raw rows into TF32 hi / lo parts; consecutive threads take
-    // consecutive rows (conflict-free 16-byte reads and writes)
+  auto worker_sync = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(kWorkers) : "memory"); };
+  // split this worker's pieces of the chunk at k0 (raw slot `slot`) into TF32 hi / lo parts in stage st
+  auto split = [&](long long k0, int slot, unsigned char* st) {
     const unsigned char* raw = raw_base + (uint32_t)slot * raw_stage_bytes;
-    const long long k0 = ch * kTcK;
-    for (int idx = tid; idx < rows * (kTcK / 4); idx += kTcThreads) {
-      const int row = idx % rows, q = idx / rows;
-      float4 x = *reinterpret_cast<const float4*>(raw + (uint32_t)row * kRawPitch + 16u * q);
+#pragma unroll
+    for (int m = 0; m < NI; ++m) {
+      if (ikind[m] == 0) continue;
+      float4 x = *reinterpret_cast<const float4*>(raw + iraw[m]);
       float4 hi, lo;
-      if (row < ma) {
+      if (ikind[m] == 1) {
         split_tf32(x.x, hi.x, lo.x);
         split_tf32(x.y, hi.y, lo.y);
         split_tf32(x.z, hi.z, lo.z);
         split_tf32(x.w, hi.w, lo.w);
-        *reinterpret_cast<float4*>(st + tile_off(row, 4 * q)) = hi;
-        if (packed) *reinterpret_cast<float4*>(st + tile_off(kPackRows + row, 4 * q)) = lo;
-        else *reinterpret_cast<float4*>(st + kTileA + tile_off(row, 4 * q)) = lo;
+        *reinterpret_cast<float4*>(st + io0[m]) = hi;
+        *reinterpret_cast<float4*>(st + io1[m]) = lo;
       } else {
-        const int j = row - ma;
-        if (g5b && k0 + 4 * q >= half_k) x = make_float4(-x.x, -x.y, -x.z, -x.w);
+        if (g5b && k0 >= iglim[m]) x = make_float4(-x.x, -x.y, -x.z, -x.w);
         const float4 xt = make_float4(x.y, -x.x, x.w, -x.z);
         float4 thi, tlo;
         split_tf32(x.x, hi.x, lo.x);
@@ -291,46 +329,118 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         split_tf32(xt.y, thi.y, tlo.y);
         split_tf32(xt.z, thi.z, tlo.z);
         split_tf32(xt.w, thi.w, tlo.w);
-        unsigned char* bt = st + offB;
-        *reinterpret_cast<float4*>(bt + tile_off(j, 4 * q)) = hi;
-        *reinterpret_cast<float4*>(bt + tile_off(mb + j, 4 * q)) = thi;
-        *reinterpret_cast<float4*>(bt + tile_off(kLoRow + j, 4 * q)) = lo;
-        *reinterpret_cast<float4*>(bt + tile_off(kLoRow + mb + j, 4 * q)) = tlo;
+        *reinterpret_cast<float4*>(st + io0[m]) = hi;
+        *reinterpret_cast<float4*>(st + io1[m]) = thi;
+        *reinterpret_cast<float4*>(st + io2[m]) = lo;
+        *reinterpret_cast<float4*>(st + io3[m]) = tlo;
       }
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (tid == 0) {
-      // the descriptor's address field is addr >> 4 in its low bits (all of
-      // this CTA's shared memory stays below 2^18 bytes), so tiles and K
-      // steps are plain offsets of one base descriptor
-      const uint64_t d_a0 = smem_desc(smem_u32(st));
-      const uint64_t d_a1 = d_a0 + (kTileA >> 4), d_b = d_a0 + (offB >> 4);
+  };
+
+  // FP64 sums of the hi-column (0..31) and lo-column (32..63) accumulators of this thread's lane
+  double acc[32];
 #pragma unroll
-      for (int kk = 0; kk < kTcK / 8; ++kk) {
-        const uint64_t o = (uint64_t)kk * (256 >> 4);  // 8 floats = two core matrices along K
-        const uint32_t acc_in = (in_window > 0 || kk > 0) ? 1u : 0u;
-        tc_mma(tmem, d_a0 + o, d_b + o, acc_in);
-        if (!packed) tc_mma(tmem, d_a1 + o, d_b + o, 1u);
+  for (int i = 0; i < 32; ++i) acc[i] = 0.0;
+  int in_window = 0;  // (issuer) chunks in the current accumulation window
+  int last_stage = -1;
+  uint32_t last_parity = 0;
+  auto raise = [&]() {
+    failed = true;
+    *abort_flag = 1;
+  };
+
+  long long k0_use = (long long)blockIdx.x * kTcK;  // k0 of chunk it
+  if (worker)  // prologue: nraw - 1 chunks in flight
+    for (int p = 0; p < nraw - 1; ++p) issue(p < niter, k0_use + p * kstep, p);
+  long long k0_fill = k0_use + (long long)(nraw - 1) * kstep;  // k0 of chunk it + nraw - 1
+  int stage = 0;        // it % nstage
+  uint32_t use = 0;     // it / nstage
+  int slot = 0;         // it % nraw: raw slot of chunk it
+  int fill = nraw - 1;  // (it + nraw - 1) % nraw: raw slot of the chunk issued in iteration it
+  for (int it = 0; it < niter; ++it) {
+    unsigned char* st = stage_base + stage * kStage;
+    if (*abort_flag) failed = true;  // another thread's wait expired: skip the rest
+    if (worker) {
+      if (nraw >= 2) {
+        raw_wait();
+        worker_sync();  // every worker's copies of chunk it landed; chunk it - 1 is split (its slot is free)
+        issue(it + nraw - 1 < niter, k0_fill, fill);
+      } else {  // one raw slot: copy and split in turn
+        worker_sync();
+        issue(true, k0_use, 0);
+        cp_async_wait<0>();
+        worker_sync();
       }
-      tc_commit(smem_u32(&bars[stage]));
+      if (!failed && use >= 1 &&
+          !mbar_wait(smem_u32(&bars[stage]), (use - 1) & 1, abort_flag, stall, stall_cycles))  // stage free
+        raise();
+      if (!failed) {
+        split(k0_use, slot, st);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor core
+      }
+      __syncwarp();
+      if (!failed && lane == 0) mbar_arrive(smem_u32(&bars[4 + stage]));
+    } else if (issuer) {
+      if (!failed && !mbar_wait(smem_u32(&bars[4 + stage]), use & 1, abort_flag, stall, stall_cycles)) raise();
+      if (!failed) {
+        tc_fence_after();
+        // the descriptor's address field is addr >> 4 in its low bits (all of
+        // this CTA's shared memory stays below 2^18 bytes), so tiles and K
+        // steps are plain offsets of one base descriptor
+        const uint64_t d_a0 = smem_desc(smem_u32(st));
+        const uint64_t d_a1 = d_a0 + (kTileA >> 4), d_b = d_a0 + (offB >> 4);
+#pragma unroll
+        for (int kk = 0; kk < kTcK / 8; ++kk) {
+          const uint64_t o = (uint64_t)kk * (256 >> 4);  // 8 floats = two core matrices along K
+          const uint32_t acc_in = (in_window > 0 || kk > 0) ? 1u : 0u;
+          tc_mma(tmem, d_a0 + o, d_b + o, acc_in);
+          if (!packed) tc_mma(tmem, d_a1 + o, d_b + o, 1u);
+        }
+        tc_commit(smem_u32(&bars[stage]));
+        last_stage = stage;
+        last_parity = use & 1;
+      }
+      ++in_window;
     }
-    last_stage = stage;
-    last_parity = use & 1;
-    ++it;
-    ++in_window;
-    if (in_window == kFlush) flush();
+    if ((it + 1) % kFlush == 0 || it + 1 == niter) {
+      // window complete: its last commit covers every MMA issued so far
+      if (issuer && !failed && last_stage >= 0 &&
+          !mbar_wait(smem_u32(&bars[last_stage]), last_parity, abort_flag, stall, stall_cycles))
+        raise();
+      __syncthreads();
+      if (*abort_flag) failed = true;  // uniform: no thread writes the flag between the two barriers
+      tc_fence_after();
+      if (!failed && warp < 4) {
+        float v[32];
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        tc_load32(lane_base, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[i] += (double)v[i];
+        tc_load32(lane_base + kLoRow, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[i] += (double)v[i];
+      }
+      tc_fence_before();
+      __syncthreads();
+      in_window = 0;
+    }
+    if (++stage == nstage) {
+      stage = 0;
+      ++use;
+    }
+    if (++slot == nraw) slot = 0;
+    if (++fill == nraw) fill = 0;
+    k0_use += kstep;
+    k0_fill += kstep;
   }
-  cp_async_wait<0>();  // no copy may still target shared memory when the CTA exits
-  if (!failed) flush();
-  if (failed) {
+  if (worker) cp_async_wait<0>();  // no copy may still target shared memory when the CTA exits
+  const bool any_failed = __syncthreads_or(failed || *abort_flag != 0);
+  if (any_failed) {
     if (tid == 0) atomicExch(err, 1);
-    // bounded wait (no stall) for this CTA's own MMAs before releasing tensor memory
-    if (last_stage >= 0) mbar_wait(smem_u32(&bars[last_stage]), last_parity);
+    // bounded wait (no stall, no abort) for this CTA's own MMAs before releasing tensor memory
+    if (issuer && last_stage >= 0) mbar_wait(smem_u32(&bars[last_stage]), last_parity, nullptr);
   }
-  if (!failed && packed) {
+  if (!any_failed && packed) {
     // lanes 64 + i hold the lo.hi and lo.lo products of row i: add them into lane i
     // (the stages are free: the last flush waited for every MMA)
     double* fold = reinterpret_cast<double*>(stage_base);
@@ -344,7 +454,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int i = 0; i < 32; ++i) acc[i] += fold[tid * 33 + i];
     }
   }
-  if (!failed && warp < 4) {
+  if (!any_failed && warp < 4) {
     const int row = tid;  // warps 0-3: lane quarter = rows 0..127
     if (row < ma) {  // acc[j] = Re, acc[mb + j] = Im of C_row,j (static indices keep acc in registers)
       double* pd = reinterpret_cast<double*>(partial);
@@ -370,13 +480,21 @@ int tc_gram_max_rhs() { return kLoRow / 2; }
 cudaError_t launch_tc_gram(const void* A, int ma, const void* B, int mb, int64_t V, int g5b, double2* partial,
                            int nblk, int* err, const int* stall, long long stall_cycles, cudaStream_t st) {
   if (ma < 1 || ma > kTcM || mb < 1 || 2 * mb > kLoRow) return cudaErrorInvalidValue;
-  const uint32_t nraw = raw_stages(ma, ma + mb);
-  const uint32_t smem = 2 * stage_bytes(ma) + kCtrl + nraw * (uint32_t)(ma + mb) * kRawPitch;
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_tc_gram<<<nblk, kTcThreads, smem, st>>>(static_cast<const float*>(A), ma, static_cast<const float*>(B), mb,
-                                            24LL * V, g5b, partial, err, (int)nraw, stall, stall_cycles);
-  return cudaGetLastError();
+  const int nstage = mma_stages(ma, ma + mb);
+  const uint32_t nraw = raw_stages(ma, ma + mb, nstage);
+  const uint32_t smem = (uint32_t)nstage * stage_bytes(ma) + kCtrl + nraw * (uint32_t)(ma + mb) * kRawPitch;
+  const int nitem = ((ma + mb + 7) / 8) * 128;
+  const int ni = (nitem + kWorkers - 1) / kWorkers;  // <= 5 for 144 rows
+  auto run = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<nblk, kTcThreads, smem, st>>>(static_cast<const float*>(A), ma, static_cast<const float*>(B), mb,
+                                         24LL * V, g5b, partial, err, nstage, (int)nraw, stall, stall_cycles);
+    return cudaGetLastError();
+  };
+  if (ni <= 2) return run(k_tc_gram<2>);
+  if (ni <= 3) return run(k_tc_gram<3>);
+  return run(k_tc_gram<5>);
 }
 
 }  // namespace ov

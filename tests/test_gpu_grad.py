@@ -29,12 +29,13 @@ def _gpu_grad(dims, links, chi, order, a, b, prec, antiperiodic=False, grad_mem=
 @pytest.mark.parametrize("order", [1, 2, 15, 16, 17, 40])
 @pytest.mark.parametrize("antiperiodic", [False, True])
 @pytest.mark.parametrize("keep_all", [True, False])
-@pytest.mark.parametrize("dims", [(4, 2, 4, 2), (4, 4, 4, 2)])
+@pytest.mark.parametrize("dims", [(4, 2, 4, 2), (4, 4, 4, 2), (8, 4, 2, 2)])
 def test_grad_matches_oracle(order, antiperiodic, keep_all, dims):
     """Both sweeps: every recurrence term kept (default allowance) and
     checkpoints every 16 terms with recomputation (allowance 0).  4x2x4x2 runs
-    the per-site force kernel, 4x4x4x2 the shared-memory tiled one (FP32 box
-    4x4x4x2: one block, the t faces wrapping onto the box; FP64 box 4x4x2x2)."""
+    the per-site force kernel in both precisions; the shared-memory tiled one
+    runs for FP64 (box 4x4x2x2) on 4x4x4x2 and 8x4x2x2 and for FP32 (box
+    8x4x2x2: one block, every face wrapping onto the box) on 8x4x2x2."""
     links = inputs.gauge_links(dims, seed=7001)
     chi = inputs.gaussian_source(dims, seed=7002)
     a, b = 0.4, 6.6
