@@ -7,8 +7,10 @@ builds the seeded links (exp(i 0.3 H)), takes n_ev orthonormal vectors from a
 single Rayleigh-Ritz pass of ov_eigs (the same amount of deflation work as
 converged eigenvectors; the eigensolver itself is left out of the profile),
 configures sign(K) on [lo, hi] and runs `applies` sign(K) applications (or
-D^dagger D solves with --solve, GMRESR solves of D x = b with --gmresr), all
-through the C ABI.  --eigs-tol converges the eigenpairs instead (n_ev + 1 of
+D^dagger D solves with --solve, GMRESR solves of D x = b with --gmresr, or
+gradients of chi^dagger P(K) chi with respect to the links with --grad, on an
+FP32 or FP64 context, P(K) the undeflated order-`order` polynomial on
+[lo, hi]), all through the C ABI.  --eigs-tol converges the eigenpairs instead (n_ev + 1 of
 them; the interval then becomes [|lambda_{n_ev+1}|, lambda_max]).
 --profile-range brackets the timed loop with cudaProfilerStart/Stop, so that
 `ncu --profile-from-start off` sees only those launches.
@@ -22,8 +24,8 @@ def main(argv=None):
     import torch
 
     from . import inputs
-    from .binding import (Ctx, ov_eigs, ov_get_stats, ov_reset_stats, ov_set_profiling, ov_sign_apply, ov_solve,
-                          ov_solve_gmresr)
+    from .binding import (Ctx, ov_eigs, ov_get_stats, ov_reset_stats, ov_set_profiling, ov_sign_apply,
+                          ov_sign_poly_grad, ov_solve, ov_solve_gmresr)
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--lattice", default="24,24,24,48")
@@ -36,6 +38,7 @@ def main(argv=None):
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--solve", action="store_true")
     ap.add_argument("--gmresr", action="store_true")
+    ap.add_argument("--grad", action="store_true")
     ap.add_argument("--eigs-tol", type=float, default=None)
     ap.add_argument("--profile-range", action="store_true")
     ap.add_argument("--mu", type=float, default=0.02)
@@ -64,6 +67,11 @@ def main(argv=None):
     with Ctx(dims, links, args.prec) as c:
         c.sign_config(args.order, lo, hi, evals, evecs)
         out = torch.empty_like(psi)
+        if args.grad:
+            if args.prec not in ("fp32", "fp64") or args.nrhs != 1:
+                raise SystemExit("--grad needs --prec fp32 or fp64 and one right-hand side")
+            chi = psi.to(torch.complex64) if args.prec == "fp32" else psi
+            grad = torch.empty((4,) + fshape[:4] + (3, 3), dtype=torch.complex128, device="cuda")
         if args.profile and not args.solve:
             ov_sign_apply(c.handle, psi, out, args.nrhs)  # tunes the stencil shape for nrhs
             torch.cuda.synchronize()
@@ -77,6 +85,8 @@ def main(argv=None):
             if args.solve:
                 it, res = ov_solve(c.handle, args.mu, 1e-10, 20000, psi, out, args.nrhs, allow_not_converged=True)
                 print(f"solve: {it} iterations, true residual {res:.3e}")
+            elif args.grad:
+                ov_sign_poly_grad(c.handle, args.order, lo, hi, chi, grad)
             elif args.gmresr:
                 it, res = ov_solve_gmresr(c.handle, args.mu, 1e-10, 100000, psi, out, args.nrhs,
                                           allow_not_converged=True)
@@ -93,7 +103,8 @@ def main(argv=None):
             per = st["dslash_ms"] / max(1, st["dslash_timed"]) * 1e3
             print(f"stencil: {per:.2f} us per launch ({per / args.nrhs:.2f} per RHS) over {st['dslash_timed']} "
                   f"recurrence launches", flush=True)
-        what = "solve" if args.solve else "gmresr solve" if args.gmresr else "sign apply"
+        what = ("solve" if args.solve else "gmresr solve" if args.gmresr else "gradient" if args.grad
+                else "sign apply")
         print(f"{args.applies} x {what} ({args.prec}, {args.lattice}, "
               f"order {args.order}, n_ev {args.n_ev}, nrhs {args.nrhs}): {dt / args.applies * 1e3:.2f} ms each; "
               f"stats {ov_get_stats(c.handle)}", flush=True)
