@@ -1,14 +1,18 @@
 """Full-size (24^3 x 48) checks in the launch configuration bench.py times
 (autotuned stencil, 16-bit links persisting in L2): the stencil against the
-oracle on the whole field, and sign(K) with 40 deflated pairs (from ov_eigs)
-through properties that hold at any size."""
+oracle on the whole field; sign(K) against the oracle on the whole field and
+site by site at a low Chebyshev order (the oracle's cost grows with it) with
+seeded orthonormal deflation vectors (the projected form of Eq. 3 is defined
+for any orthonormal set, and oracle inputs never come from the CUDA path);
+and sign(K) at order 256 with 40 deflated pairs from ov_eigs through
+properties that hold at any size."""
 import numpy as np
 import pytest
 
-from oracle import wilson
+from oracle import chebyshev, overlap, wilson
 from paper_1510_06897_gb300 import inputs
 from paper_1510_06897_gb300.binding import Ctx, ov_eigs
-from tests.gpu_util import dev, host, need_gpu, rel, torch
+from tests.gpu_util import dev, host, need_gpu, rel, site_rel, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -33,6 +37,40 @@ def test_stencil_full_size(links, prec, tol):
         got = host(c.kernel(dev(psi)))
     want = wilson.kernel_k(links, psi[0])[None]
     assert rel(got, want) < tol
+
+
+@pytest.fixture(scope="module")
+def oracle_sign16(links):
+    """sign(K) psi by the oracle at full size: Chebyshev order 16 on
+    [0.5, 6.5], 8 seeded orthonormal deflation vectors with sgn(lambda)
+    alternating, a Gaussian psi (33 oracle K applications)."""
+    n = 8
+    rng = np.random.default_rng(2701)
+    m = rng.standard_normal((12 * inputs.volume(DIMS), n)) + 1j * rng.standard_normal((12 * inputs.volume(DIMS), n))
+    q, _ = np.linalg.qr(m)
+    del m
+    evecs = np.ascontiguousarray(q.T).reshape((n,) + SHAPE)
+    del q
+    evals = np.array([0.31, -0.33, 0.36, -0.38, 0.41, -0.43, 0.46, -0.48])
+    a, b, order = 0.5, 6.5, 16
+    psi = inputs.gaussian_source(DIMS, seed=2702)
+    cfg = overlap.SignConfig(chebyshev.coefficients(order, a, b), a, b, evals, evecs)
+    want = overlap.sign_apply(links, psi[0], cfg)[None]
+    return dict(evecs=evecs, evals=evals, a=a, b=b, order=order, psi=psi, want=want)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp16", 1e-2)])
+def test_sign_full_size_against_oracle(links, oracle_sign16, prec, tol):
+    """The tuned full-size launch shape (and, for FP16, the L2-persisting
+    links) against the oracle: whole field and worst site."""
+    p = oracle_sign16
+    with Ctx(DIMS, dev(links), prec) as c:
+        c.sign_config(p["order"], p["a"], p["b"], p["evals"], dev(p["evecs"]))
+        got = host(c.sign(dev(p["psi"])))
+    err, serr = rel(got, p["want"]), site_rel(got, p["want"])
+    print(f"{prec}: field {err:.2e}, worst site {serr:.2e}")
+    assert err < tol
+    assert serr < 2.5 * tol
 
 
 @pytest.fixture(scope="module")
