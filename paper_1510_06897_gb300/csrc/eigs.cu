@@ -48,16 +48,19 @@ void launch_random_block(OpPrec p, void* out, int m, int64_t V, uint64_t seed, c
 // 4 x 4 tile of (i, j) pairs.  Per-chunk sums in R, running sums in FP64.
 constexpr int kGramSites = 8;
 constexpr int kGramMax = 64;  // max vectors per block (per side)
+// shared-memory row of one vector: kGramSites * 12 complex + 1 of padding, so
+// that lanes reading consecutive vectors j hit consecutive banks
+constexpr int kGramStride = kGramSites * 12 + 1;
 
 template <class T>
 __global__ void __launch_bounds__(256) k_gram(const char* __restrict__ A, int ma, const char* __restrict__ B, int mb,
                                               int64_t V, double2* __restrict__ partial, int g5b) {
   using R = typename Store<T>::R;
   extern __shared__ unsigned char smem_raw[];
-  cplx<R>* sa = reinterpret_cast<cplx<R>*>(smem_raw);                 // [ma][kGramSites*12]
-  cplx<R>* sb = sa + (size_t)kGramMax * kGramSites * 12;               // [mb][kGramSites*12]
+  cplx<R>* sa = reinterpret_cast<cplx<R>*>(smem_raw);  // [ma][kGramStride]
+  cplx<R>* sb = sa + (size_t)kGramMax * kGramStride;    // [mb][kGramStride]
   const int tid = threadIdx.x;
-  const int ti = tid / 16, tj = tid % 16;  // 16 x 16 threads, 4 x 4 pairs each
+  const int ti = tid / 16, tj = tid % 16;  // 16 x 16 threads, pairs (ti + 16 a, tj + 16 b), a, b < 4
   double2 acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -84,7 +87,7 @@ __global__ void __launch_bounds__(256) k_gram(const char* __restrict__ A, int ma
 #pragma unroll
         for (int k = 0; k < 12; ++k) x.c[k] = {R(0), R(0)};
       }
-      cplx<R>* dst = (v < ma) ? sa + ((size_t)v * kGramSites + ls) * 12 : sb + ((size_t)(v - ma) * kGramSites + ls) * 12;
+      cplx<R>* dst = ((v < ma) ? sa + (size_t)v * kGramStride : sb + (size_t)(v - ma) * kGramStride) + ls * 12;
 #pragma unroll
       for (int k = 0; k < 12; ++k) dst[k] = x.c[k];
     }
@@ -98,13 +101,13 @@ __global__ void __launch_bounds__(256) k_gram(const char* __restrict__ A, int ma
       cplx<R> av[4], bv[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        const int i = ti * 4 + a;
-        av[a] = (i < ma) ? sa[(size_t)i * kGramSites * 12 + e] : cplx<R>{R(0), R(0)};
+        const int i = ti + 16 * a;
+        av[a] = (i < ma) ? sa[(size_t)i * kGramStride + e] : cplx<R>{R(0), R(0)};
       }
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        const int j = tj * 4 + b;
-        bv[b] = (j < mb) ? sb[(size_t)j * kGramSites * 12 + e] : cplx<R>{R(0), R(0)};
+        const int j = tj + 16 * b;
+        bv[b] = (j < mb) ? sb[(size_t)j * kGramStride + e] : cplx<R>{R(0), R(0)};
       }
 #pragma unroll
       for (int a = 0; a < 4; ++a)
@@ -123,14 +126,14 @@ __global__ void __launch_bounds__(256) k_gram(const char* __restrict__ A, int ma
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      const int i = ti * 4 + a, j = tj * 4 + b;
+      const int i = ti + 16 * a, j = tj + 16 * b;
       if (i < ma && j < mb) partial[((int64_t)i * mb + j) * gridDim.x + blockIdx.x] = acc[a][b];
     }
 }
 
 size_t gram_smem_bytes(OpPrec p) {
   const size_t c = (p == OP_F64) ? 16 : 8;
-  return 2 * (size_t)kGramMax * kGramSites * 12 * c;
+  return 2 * (size_t)kGramMax * kGramStride * c;
 }
 
 int gram_max_vectors() { return kGramMax; }
@@ -157,9 +160,12 @@ template <class T>
 __global__ void k_rotate(const char* __restrict__ Y, int m_in, const double2* __restrict__ Q, int m_out,
                          char* __restrict__ out, int64_t V) {
   using R = typename Store<T>::R;
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // block b: output tile b % ntj, site tile b / ntj, so that the blocks of one
+  // site tile run together and read each input chunk through L2 once
+  const int ntj = (m_out + kRotJ - 1) / kRotJ;
+  const int64_t s = (int64_t)(blockIdx.x / ntj) * blockDim.x + threadIdx.x;
   if (s >= V) return;
-  const int j0 = blockIdx.y * kRotJ;
+  const int j0 = (int)(blockIdx.x % ntj) * kRotJ;
   const int64_t vbytes = (int64_t)Store<T>::bytes_per_site * V;
   Spinor<R> acc[kRotJ];
 #pragma unroll
@@ -186,7 +192,7 @@ __global__ void k_rotate(const char* __restrict__ Y, int m_in, const double2* __
 
 void launch_rotate(OpPrec p, const void* Y, int m_in, const double2* Q, int m_out, void* out, int64_t V,
                    cudaStream_t st) {
-  dim3 grid((unsigned)((V + 127) / 128), (unsigned)((m_out + kRotJ - 1) / kRotJ));
+  const unsigned grid = (unsigned)(((V + 127) / 128) * ((m_out + kRotJ - 1) / kRotJ));
   if (p == OP_F64)
     k_rotate<F64><<<grid, 128, 0, st>>>(static_cast<const char*>(Y), m_in, Q, m_out, static_cast<char*>(out), V);
   else

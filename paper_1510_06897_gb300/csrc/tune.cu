@@ -15,7 +15,9 @@
 namespace ov {
 
 // Times one stencil variant on nrhs right-hand sides: a K step and a
-// recurrence step (three extra vector reads), after one warm-up pair.
+// recurrence step (three extra vector reads), after one warm-up pair; three
+// such pairs per run for short launches, one for long ones (several right-
+// hand sides, or the ALU-bound FP64 kernel at ~1 ms a launch).
 ov_status time_variant(ov_ctx* c, Inst& I, const DslashCfg& cfg, const void* links, int nrhs, DevBuf* buf,
                        cudaEvent_t e0, cudaEvent_t e1, float* ms) {
   EpiArgs ek;
@@ -29,7 +31,7 @@ ov_status time_variant(ov_ctx* c, Inst& I, const DslashCfg& cfg, const void* lin
   er.w[2] = 0.25;
   for (int rep = 0; rep < 2; ++rep) {
     if (rep == 1) OV_CK(cudaEventRecord(e0, c->st));
-    for (int k = 0; k < (nrhs > 4 ? 1 : 3); ++k) {
+    for (int k = 0; k < ((nrhs > 4 || I.p == OP_F64) ? 1 : 3); ++k) {
       if (!launch_dslash(I.p, I.p, cfg, c->g, links, buf[0].p, buf[1].p, ek, nrhs, c->st) ||
           !launch_dslash(I.p, I.p, cfg, c->g, links, buf[1].p, buf[3].p, er, nrhs, c->st))
         return fail(c, OV_ERR_CUDA, "stencil variant not compiled");

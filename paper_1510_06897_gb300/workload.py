@@ -56,7 +56,12 @@ def main(argv=None):
     if args.n_ev > 0 and args.eigs_tol is not None:
         ev = torch.zeros((args.n_ev + 1,) + fshape, dtype=torch.complex128, device="cuda")
         with Ctx(dims, links, "fp32" if args.prec != "fp64" else "fp64") as c:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             evals, hi = ov_eigs(c.handle, args.n_ev + 1, args.eigs_tol, 3000, ev)
+            torch.cuda.synchronize()
+            print(f"ov_eigs: {args.n_ev + 1} pairs to {args.eigs_tol} in {time.perf_counter() - t0:.2f} s, "
+                  f"{ov_get_stats(c.handle)['inner_iterations']} filter + Rayleigh-Ritz steps", flush=True)
         lo = float(abs(evals[args.n_ev]))
         evals, evecs = evals[:args.n_ev].copy(), ev[:args.n_ev].contiguous()
         del ev
