@@ -123,8 +123,9 @@ __device__ __forceinline__ void cp_wait_group() { asm volatile("cp.async.wait_gr
 // copied into shared memory once with cp.async, three stages deep (pairs
 // p + 1 and p + 2 land while pair p is used; one barrier per pair), so each
 // vector leaves L2 about
-// (box + faces) / box times (2.4 for 8 x 4 x 2 x 2: rows of 8 sites are whole
-// 128-byte lines of each FP32 chunk array) instead of once for the
+// (box + faces) / box times (2.6 for the FP32 box 8 x 2 x 2 x 2: rows of 8
+// sites are whole 128-byte lines of each FP32 chunk array, and two 256-thread
+// blocks fit on an SM) instead of once for the
 // site and once more for every direction that reaches it from outside the
 // block.  The pairs are folded in the same order with the same arithmetic as
 // k_force_pairs.
@@ -138,6 +139,8 @@ struct ForceTile {
   static constexpr int NS = 3;                                   // stages
   static constexpr int SMEM = NS * STAGE + NE * 4;               // stages + site table
   static constexpr int NT = 4 * NB;                              // threads
+  // two resident blocks per SM (<= 128 registers) when their shared memory fits
+  static constexpr int MINB = (NT < 512 && 2 * (SMEM + 1024) <= 228 * 1024) ? 2 : 1;
   static constexpr int NI = (2 * CH * NE + NT - 1) / NT;         // copy items per thread and pair
   static bool fits(const LatticeH& g) {
     return g.L[0] % BX == 0 && g.L[1] % BY == 0 && g.L[2] % BZ == 0 && g.L[3] % BT == 0;
@@ -212,7 +215,7 @@ __device__ __forceinline__ void force_tile_store(const Lattice& g, const void* l
 }
 
 template <class T, int BX, int BY, int BZ, int BT>
-__global__ void __launch_bounds__(4 * BX * BY * BZ * BT, 1)
+__global__ void __launch_bounds__(ForceTile<T, BX, BY, BZ, BT>::NT, ForceTile<T, BX, BY, BZ, BT>::MINB)
     k_force_tile(Lattice g, const void* __restrict__ links, PairArgsDev<typename Store<T>::R> P, void* Gv) {
   using R = typename Store<T>::R;
   using TG = ForceTile<T, BX, BY, BZ, BT>;
@@ -366,7 +369,7 @@ void launch_force_pairs(OpPrec p, const LatticeH& gh, const void* links, const F
   } else {
     PairArgsDev<float> P;
     args(&P);
-    if (ForceTile<F32, 8, 4, 2, 2>::fits(gh)) launch_force_tile<F32, 8, 4, 2, 2>(g, links, P, G, st);
+    if (ForceTile<F32, 8, 2, 2, 2>::fits(gh)) launch_force_tile<F32, 8, 2, 2, 2>(g, links, P, G, st);
     else k_force_pairs<F32><<<grid, 128, 0, st>>>(g, links, P, G);
   }
 }

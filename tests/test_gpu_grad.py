@@ -35,7 +35,7 @@ def test_grad_matches_oracle(order, antiperiodic, keep_all, dims):
     checkpoints every 16 terms with recomputation (allowance 0).  4x2x4x2 runs
     the per-site force kernel in both precisions; the shared-memory tiled one
     runs for FP64 (box 4x4x2x2) on 4x4x4x2 and 8x4x2x2 and for FP32 (box
-    8x4x2x2: one block, every face wrapping onto the box) on 8x4x2x2."""
+    8x2x2x2: two blocks, the z and t faces wrapping onto the box) on 8x4x2x2."""
     links = inputs.gauge_links(dims, seed=7001)
     chi = inputs.gaussian_source(dims, seed=7002)
     a, b = 0.4, 6.6
