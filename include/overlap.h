@@ -370,8 +370,7 @@ ov_status ov_reset_stats(ov_ctx* ctx);
  * (each call writes everything it reads, so nothing needs clearing): calls
  * that may overlap on the GPU race and must be serialised by the caller.  The
  * first call on a device looks up the array's address with that device
- * current and caches it; make that first call before any stream capture.
- * Error text: ov_last_error(NULL). */
+ * current and caches it.  Error text: ov_last_error(NULL). */
 ov_status ov_wilson_noalloc(const int dims[4], const void* links, const void* in, void* out, int nrhs,
                             ov_dtype dtype, int antiperiodic_t, void* cuda_stream);
 

@@ -19,8 +19,7 @@
 //     byte a call reads from the array is written earlier in the same call,
 //     so nothing has to be cleared between calls.
 //   * the first call on each device looks up the array's device address
-//     (cudaGetSymbolAddress, with that device current) and caches it; make
-//     that first call before any stream capture.
+//     (cudaGetSymbolAddress, with that device current) and caches it.
 #include <cmath>
 #include <mutex>
 #include <string>
