@@ -206,9 +206,12 @@ __global__ void __launch_bounds__(kReduceThreads) k_defl_dot(const char* __restr
   __shared__ double2 smem[32];
   const int64_t evec_bytes = (int64_t)Store<TE>::bytes_per_site * V;
   for (int i0 = 0; i0 < n_ev; i0 += kDeflChunk) {
-    double2 acc[kDeflChunk];
+    // a thread's few sites (V / (grid x block), ~4 at 24^3 x 48) are summed in
+    // the arithmetic type and converted to FP64 once, so that FP32 vectors keep
+    // the slow FP64 pipe out of the site loop (for FP64 the sum is unchanged)
+    cplx<R> acc[kDeflChunk];
 #pragma unroll
-    for (int j = 0; j < kDeflChunk; ++j) acc[j] = make_double2(0.0, 0.0);
+    for (int j = 0; j < kDeflChunk; ++j) acc[j] = {R(0), R(0)};
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < V; s += (int64_t)gridDim.x * blockDim.x) {
       Spinor<R> x;
       load_spinor_as<TS, R>(psi, s, V, x);
@@ -224,15 +227,14 @@ __global__ void __launch_bounds__(kReduceThreads) k_defl_dot(const char* __restr
           cplx<R> d = {R(0), R(0)};
 #pragma unroll
           for (int k = 0; k < 12; ++k) d = d + cmulc(f.c[k], x.c[k]);
-          acc[j].x += (double)d.re;
-          acc[j].y += (double)d.im;
+          acc[j] = acc[j] + d;
         }
       }
     }
 #pragma unroll
     for (int j = 0; j < kDeflChunk; ++j) {
       if (i0 + j < n_ev) {
-        double2 r = block_sum(acc[j], smem);
+        double2 r = block_sum(make_double2((double)acc[j].re, (double)acc[j].im), smem);
         if (threadIdx.x == 0) partial[(int64_t)(i0 + j) * gridDim.x + blockIdx.x] = r;
       }
     }
