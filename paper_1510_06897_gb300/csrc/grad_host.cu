@@ -2,8 +2,8 @@
 // links, P(K) = K f_N(K^2) the undeflated polynomial of Eq. 3.
 //
 // Forward: the Clenshaw recurrence b_k = c_k chi + 2 Z b_{k+1} - b_{k+2}
-// (k = N..0), g = (b_0 - b_2)/2, S = (K chi)^dagger g, keeping (b_k) for
-// k = 1, 2 mod 16 as checkpoints.  Reverse: with gbar = K chi the adjoint
+// (k = N..0), g = (b_0 - b_2)/2, S = (K chi)^dagger g, keeping all its terms
+// or checkpoints of them (below).  Reverse: with gbar = K chi the adjoint
 // vectors obey bbar_0 = gbar/2, bbar_1 = 2 Z bbar_0,
 // bbar_2 = 2 Z bbar_1 - bbar_0 - gbar/2, bbar_j = 2 Z bbar_{j-1} - bbar_{j-2},
 // and
