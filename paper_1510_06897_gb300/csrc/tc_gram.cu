@@ -21,20 +21,21 @@
 //
 // Pipeline per CTA (512 threads, warp-specialised): 15 worker warps copy raw
 // 64-float chunks of every row into a ring of up to six shared-memory
-// buffers with cp.async (several chunks in flight), each lane owning the
-// same 16-byte pieces of every chunk, so it reads back only its own copies
-// and no CTA barrier guards the ring; they split the pieces into TF32 hi / lo
-// parts in one of two or three MMA stages (canonical no-swizzle K-major
-// layout, 8-row x 16-byte core matrices) and arrive on the stage's "filled"
-// mbarrier.  Lane 0 of the last warp waits on it, issues the chunk's 8 (or
-// 16) MMAs and commits them to the stage's "consumed" mbarrier, which the
-// workers wait on before refilling the stage.  The CTA synchronises only when
-// it moves the tensor-memory accumulator into FP64 registers (every 64
-// chunks).  Every mbarrier wait is bounded (about a second); on expiry a
-// thread raises a shared abort flag, every thread runs the rest of its
-// iterations without work (so the flush barriers still match), the kernel
-// records an error flag, waits (bounded) for its own copies and MMAs in
-// flight, frees its tensor memory and returns.
+// buffers with cp.async (sixteen lanes per row's 256 bytes; several chunks in
+// flight), meet at a named barrier of the worker warps once a chunk has
+// landed, and split their fixed 16-byte pieces (eight consecutive lanes on
+// eight consecutive rows) into TF32 hi / lo parts in one of two or three MMA
+// stages (canonical no-swizzle K-major layout, 8-row x 16-byte core
+// matrices), then arrive on the stage's "filled" mbarrier.  Lane 0 of the
+// last warp waits on it, issues the chunk's 8 (or 16) MMAs and commits them
+// to the stage's "consumed" mbarrier, which the workers wait on before
+// refilling the stage.  The whole CTA synchronises only when it moves the
+// tensor-memory accumulator into FP64 registers (every 64 chunks).  Every
+// mbarrier wait is bounded (about a second); on expiry a thread raises a
+// shared abort flag, every thread runs the rest of its iterations without
+// work (so the barriers still match), the kernel records an error flag,
+// waits (bounded) for its own copies and MMAs in flight, frees its tensor
+// memory and returns.
 #include "common.cuh"
 #include "internal.h"
 
